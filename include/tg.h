@@ -1,0 +1,210 @@
+/*
+ * tg.h -- C-ABI of the device-resident task-graph executor (libtg.so).
+ *
+ * A graph mixes static tasks and condition tasks (Taskflow paper, section
+ * "Conditional Tasking").  Edges out of a condition task are WEAK, all other
+ * edges are STRONG (section "Scheduling Condition Tasks").  Execution starts
+ * at the tasks with zero strong and zero weak in-edges; a task runs when its
+ * remaining strong dependencies reach zero; a condition task returns an index
+ * into its successors, counted in the order the edges were inserted, and
+ * control jumps straight to that successor without touching any join counter
+ * (Algorithm 4, execute_task).  The whole run -- join counters, condition
+ * dispatch, work stealing -- happens inside one persistent CUDA kernel.
+ *
+ * Task payloads (the paper leaves task callables to the user): every task
+ * computes a deterministic 32-bit value
+ *     x = P(id, iter, insum, rounds)
+ * where id is the task's index in its graph, iter its own prior execution
+ * count, insum the 32-bit sum of the outputs delivered to this activation
+ * (each strong predecessor delivers its output when it releases the edge, a
+ * condition delivers its output to the successor it selects, a source gets
+ * 0) and rounds comes from the task's parameter word.  Per task the library
+ * keeps out (last x), cnt (executions) and dig (dig = mix(dig ^ x) per
+ * execution, from 0).
+ *
+ * Conventions for every entry point
+ *   - Returns a status int: TG_OK (0), TG_PENDING (1, tg_poll only) or a
+ *     negative TG_ERR_*.  Nothing is thrown across the ABI.
+ *   - Host input arrays are read during the call and never retained: the
+ *     caller keeps ownership.
+ *   - The device arena and the CUDA stream given to tg_ctx_create belong to
+ *     the caller (e.g. a torch uint8 tensor and torch.cuda.Stream.cuda_stream)
+ *     and must outlive the context.  The library sub-allocates the arena and
+ *     never calls cudaMalloc for graph data.
+ *   - tg_ctx / tg_graph / tg_batch handles are owned by the library until the
+ *     matching destroy call.  Calls on one context must not be made
+ *     concurrently from several host threads.
+ *   - All device work is enqueued on the context's stream.
+ */
+#ifndef TG_H
+#define TG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tg_ctx tg_ctx;
+typedef struct tg_graph tg_graph;
+typedef struct tg_batch tg_batch;
+
+/* Task kinds (Conditional Tasking).  Parameter word of every task:
+ *   bits 0-15  rounds of the payload's mixing loop
+ *   bits 16-23 trip count T of a TG_COND_LOOP (1..255)
+ *   bits 24-31 signed 8-bit return value of a TG_COND_CONST
+ * Condition return values (iter = the condition's own prior executions,
+ * nsucc = its out-degree, HC = seeded hash of (graph seed, id, iter)):
+ *   TG_COND_BRANCH  HC mod nsucc
+ *   TG_COND_LOOP    0 (loop back) unless (iter+1) mod T == 0, then the exit
+ *                   index: 1 if nsucc <= 2, else 1 + HC mod (nsucc-1)
+ *   TG_COND_CONST   the constant; an index outside [0, nsucc) schedules
+ *                   nothing (that control path ends). */
+enum { TG_STATIC = 0, TG_COND_BRANCH = 1, TG_COND_LOOP = 2, TG_COND_CONST = 3 };
+
+enum {
+    TG_OK = 0,
+    TG_PENDING = 1,          /* tg_poll: the submission has not finished */
+    TG_ERR_INVALID = -1,     /* bad argument, index out of range, limit exceeded */
+    TG_ERR_NO_SOURCE = -2,   /* no task with zero strong and zero weak in-edges */
+    TG_ERR_EDGE_KIND = -3,   /* explicit weak[] disagrees with the source task's kind */
+    TG_ERR_BUDGET = -4,      /* graph does not fit the memory budget / pools */
+    TG_ERR_RACE = -5,        /* a task was activated while already queued or running */
+    TG_ERR_EXEC_LIMIT = -6,  /* more executions than the per-graph cap */
+    TG_ERR_TIMEOUT = -7,     /* the device-side time limit expired */
+    TG_ERR_CANCELLED = -8,   /* tg_cancel was called while the graph ran */
+    TG_ERR_CUDA = -9,        /* a CUDA runtime call failed */
+    TG_ERR_INTERNAL = -10,   /* a bounded device wait gave up (scheduler fault) */
+    TG_ERR_BUSY = -11        /* the graph is already submitted and not finished */
+};
+
+/* Option flags. */
+#define TG_OPT_NO_RACE_CHECK 0x1u   /* skip the per-activation in-flight check */
+
+/* Context options; a zero field selects the default (in brackets). */
+typedef struct {
+    int32_t worker_blocks;     /* persistent blocks [SMs x resident blocks per SM] */
+    int32_t warps_per_block;   /* worker warps per block [8] */
+    int32_t deque_depth;       /* entries of each block's public deque, power of 2 [4096] */
+    int32_t steal_policy;      /* 0 random victims, 1 neighbour ring [0] */
+    int32_t max_steal;         /* victims tried per steal round [8] */
+    int32_t smem_ring;         /* entries of each block's shared-memory ready ring, power of 2 [1024] */
+    uint32_t flags;            /* TG_OPT_* */
+    uint32_t idle_sleep_ns;    /* wait of an idle warp that is not its block's thief [256] */
+    int32_t max_thieves;       /* blocks allowed to steal / poll at the same time [16] */
+    int32_t reserved;
+    uint64_t time_limit_ns;    /* device time limit per launch [10 s] */
+    uint64_t exec_cap;         /* executions per graph before TG_ERR_EXEC_LIMIT [2^31] */
+    uint64_t mem_budget_bytes; /* admission budget for graph memory [the node/edge pools] */
+    uint64_t max_nodes;        /* node pool capacity [derived from the arena] */
+    uint64_t max_edges;        /* edge pool capacity [derived from the arena] */
+} tg_ctx_opts;
+
+/* Create a context on the current CUDA device.
+ *   dev_arena, arena_bytes  caller-owned device memory (256-byte aligned)
+ *   cuda_stream             cudaStream_t the library enqueues on (NULL = legacy)
+ *   opts                    may be NULL (all defaults)
+ * Errors: TG_ERR_INVALID (NULL out, misaligned or too small arena),
+ *         TG_ERR_CUDA. */
+int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream,
+                  const tg_ctx_opts *opts, tg_ctx **out);
+int tg_ctx_destroy(tg_ctx *ctx);
+
+/* Ingest, validate and pack a graph, then copy it to the device (section
+ * "Scheduling Condition Tasks" for the strong/weak rule; Algorithm 8 for the
+ * source set).
+ *   n_nodes, kinds[n], params[n]   tasks (kinds TG_*; params as above)
+ *   n_edges, src[m], dst[m]        edges src[i] -> dst[i] in insertion order;
+ *                                  duplicates allowed, counted per edge
+ *   weak[m]                        NULL, or explicit edge kinds that must equal
+ *                                  "source task is a condition"
+ *   seed                           graph seed of the condition hash
+ * Validation order: TG_ERR_INVALID (unknown kind, index >= n, a condition
+ * without successors, loop trip 0, out-degree or strong in-degree > 65535,
+ * n == 0), then TG_ERR_EDGE_KIND, then TG_ERR_NO_SOURCE; TG_ERR_BUDGET if
+ * the pools cannot hold it.  Packing: successors in insertion order, 32-byte
+ * node records, strong in-degree per task, the source list. */
+int tg_graph_create(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
+                    uint32_t n_edges, const uint32_t *src, const uint32_t *dst,
+                    const uint8_t *weak, uint32_t seed, tg_graph **out);
+int tg_graph_destroy(tg_ctx *ctx, tg_graph *g);
+
+typedef struct {
+    uint32_t n_nodes, n_edges, n_sources, n_conditions;
+    uint64_t device_bytes;     /* pool bytes held by the graph */
+    uint64_t pack_ns;          /* host time of validation + packing */
+    uint64_t upload_ns;        /* host time of the host-to-device copy */
+} tg_graph_info;
+int tg_graph_get_info(const tg_graph *g, tg_graph_info *info);
+
+/* Run one graph: re-arm its state, launch the persistent scheduler on the
+ * context stream and wait.  Returns the graph's final status (TG_OK, or
+ * TG_ERR_RACE / EXEC_LIMIT / TIMEOUT / CANCELLED / INTERNAL / CUDA). */
+int tg_run(tg_ctx *ctx, tg_graph *g);
+
+/* Asynchronous form: enqueue the run and return at once.  *ticket names the
+ * submission for tg_poll / tg_wait.  TG_ERR_BUSY if g is still in flight. */
+int tg_submit(tg_ctx *ctx, tg_graph *g, uint64_t *ticket);
+/* Never blocks: TG_PENDING while the run is in flight, else its status. */
+int tg_poll(tg_ctx *ctx, uint64_t ticket);
+/* Blocks until the submission finished; returns its status. */
+int tg_wait(tg_ctx *ctx, uint64_t ticket);
+
+/* Ask the device to stop: running graphs end with TG_ERR_CANCELLED (the
+ * workers poll a host-mapped flag; the flag is cleared at the next launch). */
+int tg_cancel(tg_ctx *ctx);
+
+/* Copy the per-task results of g's last run to host arrays of n entries
+ * (any pointer may be NULL); total_execs = sum of cnt.  Synchronises the
+ * context stream. */
+int tg_result_copy(tg_ctx *ctx, const tg_graph *g, uint32_t *out, uint32_t *cnt, uint32_t *dig,
+                   uint64_t *total_execs);
+
+/* Batches: many graphs in ONE persistent launch.  tg_batch_create writes the
+ * launch's descriptor table and captures re-arm + scheduler kernels in a CUDA
+ * graph; tg_batch_launch replays it (async); tg_batch_wait waits and writes
+ * one status per graph.  A graph may belong to several batches but must not
+ * run in two launches at once. */
+int tg_batch_create(tg_ctx *ctx, tg_graph *const *gs, uint32_t n, tg_batch **out);
+int tg_batch_launch(tg_ctx *ctx, tg_batch *b);
+int tg_batch_wait(tg_ctx *ctx, tg_batch *b, int *statuses);
+int tg_batch_destroy(tg_ctx *ctx, tg_batch *b);
+/* Convenience: create, launch, wait and destroy; statuses may be NULL.
+ * Returns TG_OK if every graph ended TG_OK, else the first error. */
+int tg_run_batch(tg_ctx *ctx, tg_graph *const *gs, uint32_t n, int *statuses);
+
+/* Scheduler counters of the context's last launch (summed over blocks). */
+typedef struct {
+    uint64_t tasks;            /* activations executed */
+    uint64_t pops_local;       /* batches taken from a block's shared-memory ring */
+    uint64_t pops_own;         /* batches taken from the block's own public deque */
+    uint64_t steal_attempts;   /* victim deques probed */
+    uint64_t steal_hits;       /* probes that returned work */
+    uint64_t inject_pops;      /* batches taken from the shared injection queue */
+    uint64_t spills;           /* batches moved from shared memory to a public deque */
+    uint64_t idle_loops;       /* warp iterations that found no work */
+    uint64_t warp_iters;       /* warp iterations that executed work */
+    uint64_t kernel_ns;        /* device time of the last scheduler launch */
+    uint32_t worker_blocks, warps_per_block;
+} tg_stats;
+int tg_ctx_get_stats(tg_ctx *ctx, tg_stats *st);
+int tg_ctx_get_opts(const tg_ctx *ctx, tg_ctx_opts *opts);
+
+/* Roofline kernels (measurement only).
+ *  tg_bench_payload: the task payload alone on `count` independent ids with
+ *    `rounds` rounds each (no scheduling); *ns = device time; *checksum =
+ *    XOR of all outputs (to compare with the oracle's payload).
+ *  tg_bench_atomics: `count` returning 64-bit atomicAdd at distinct
+ *    pseudo-random addresses over `footprint_words` 8-byte words of arena
+ *    scratch; *ns = device time. */
+int tg_bench_payload(tg_ctx *ctx, uint64_t count, uint32_t rounds, uint64_t *ns, uint32_t *checksum);
+int tg_bench_atomics(tg_ctx *ctx, uint64_t count, uint64_t footprint_words, uint64_t *ns);
+
+const char *tg_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TG_H */

@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libtg.so: the same names as the C-ABI in
+include/tg.h, argument marshalling only.  Every step of graph execution runs
+in the library's CUDA kernels; PyTorch supplies the device arena and the
+stream.  There is no CPU fallback: if libtg.so is missing or no CUDA device
+is present, the calls raise."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtg.so")
+
+TG_STATIC, TG_COND_BRANCH, TG_COND_LOOP, TG_COND_CONST = 0, 1, 2, 3
+TG_OK, TG_PENDING = 0, 1
+TG_ERR_INVALID, TG_ERR_NO_SOURCE, TG_ERR_EDGE_KIND, TG_ERR_BUDGET = -1, -2, -3, -4
+TG_ERR_RACE, TG_ERR_EXEC_LIMIT, TG_ERR_TIMEOUT, TG_ERR_CANCELLED = -5, -6, -7, -8
+TG_ERR_CUDA, TG_ERR_INTERNAL, TG_ERR_BUSY = -9, -10, -11
+TG_OPT_NO_RACE_CHECK = 0x1
+
+STATUS_NAMES = {TG_OK: "OK", TG_PENDING: "PENDING", TG_ERR_INVALID: "INVALID",
+                TG_ERR_NO_SOURCE: "NO_SOURCE", TG_ERR_EDGE_KIND: "EDGE_KIND", TG_ERR_BUDGET: "BUDGET",
+                TG_ERR_RACE: "RACE", TG_ERR_EXEC_LIMIT: "EXEC_LIMIT", TG_ERR_TIMEOUT: "TIMEOUT",
+                TG_ERR_CANCELLED: "CANCELLED", TG_ERR_CUDA: "CUDA", TG_ERR_INTERNAL: "INTERNAL",
+                TG_ERR_BUSY: "BUSY"}
+
+
+class TgError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)} ({tg_strerror(status)})")
+
+
+class tg_ctx_opts(ctypes.Structure):
+    _fields_ = [("worker_blocks", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("deque_depth", ctypes.c_int32), ("steal_policy", ctypes.c_int32),
+                ("max_steal", ctypes.c_int32), ("smem_ring", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("idle_sleep_ns", ctypes.c_uint32),
+                ("max_thieves", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("time_limit_ns", ctypes.c_uint64), ("exec_cap", ctypes.c_uint64),
+                ("mem_budget_bytes", ctypes.c_uint64), ("max_nodes", ctypes.c_uint64),
+                ("max_edges", ctypes.c_uint64)]
+
+
+class tg_graph_info(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_uint32), ("n_edges", ctypes.c_uint32),
+                ("n_sources", ctypes.c_uint32), ("n_conditions", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64), ("pack_ns", ctypes.c_uint64),
+                ("upload_ns", ctypes.c_uint64)]
+
+
+class tg_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in
+                ("tasks", "pops_local", "pops_own", "steal_attempts", "steal_hits", "inject_pops",
+                 "spills", "idle_loops", "warp_iters", "kernel_ns")] + \
+               [("worker_blocks", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_lib = None
+
+# exported symbol -> (restype, argtypes); every symbol declared in include/tg.h
+SIGNATURES = {
+    "tg_ctx_create": (ctypes.c_int, [_vp, ctypes.c_size_t, _vp, ctypes.POINTER(tg_ctx_opts),
+                                     ctypes.POINTER(_vp)]),
+    "tg_ctx_destroy": (ctypes.c_int, [_vp]),
+    "tg_graph_create": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, ctypes.POINTER(_vp)]),
+    "tg_graph_destroy": (ctypes.c_int, [_vp, _vp]),
+    "tg_graph_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(tg_graph_info)]),
+    "tg_run": (ctypes.c_int, [_vp, _vp]),
+    "tg_submit": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_u64)]),
+    "tg_poll": (ctypes.c_int, [_vp, _u64]),
+    "tg_wait": (ctypes.c_int, [_vp, _u64]),
+    "tg_cancel": (ctypes.c_int, [_vp]),
+    "tg_result_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_u64)]),
+    "tg_batch_create": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_vp)]),
+    "tg_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "tg_batch_wait": (ctypes.c_int, [_vp, _vp, _vp]),
+    "tg_batch_destroy": (ctypes.c_int, [_vp, _vp]),
+    "tg_run_batch": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
+    "tg_ctx_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tg_stats)]),
+    "tg_ctx_get_opts": (ctypes.c_int, [_vp, ctypes.POINTER(tg_ctx_opts)]),
+    "tg_bench_payload": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
+    "tg_bench_atomics": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(_u64)]),
+    "tg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libtg.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"libtg.so not built at {path}; run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(_vp)
+
+
+def _check(st, what):
+    if st != TG_OK:
+        raise TgError(st, what)
+
+
+def tg_strerror(status: int) -> str:
+    return load().tg_strerror(status).decode()
+
+
+def tg_ctx_create(dev_arena_ptr: int, arena_bytes: int, cuda_stream: int, opts: tg_ctx_opts | None = None):
+    out = _vp()
+    st = load().tg_ctx_create(_vp(dev_arena_ptr), arena_bytes, _vp(cuda_stream),
+                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(out))
+    _check(st, "tg_ctx_create")
+    return out.value
+
+
+def tg_ctx_destroy(ctx):
+    return load().tg_ctx_destroy(_vp(ctx))
+
+
+def tg_graph_create(ctx, kinds, params, src, dst, seed=0, weak=None):
+    """Returns (status, handle); handle is None unless status == TG_OK."""
+    k, kp = _arr(kinds, np.uint8)
+    p, pp = _arr(params, np.uint32)
+    s, sp = _arr(src, np.uint32)
+    d, dp = _arr(dst, np.uint32)
+    wp = None
+    if weak is not None:
+        w, wp = _arr(weak, np.uint8)
+    out = _vp()
+    st = load().tg_graph_create(_vp(ctx), k.shape[0], kp, pp, s.shape[0], sp, dp, wp, seed & 0xFFFFFFFF,
+                                ctypes.byref(out))
+    return st, (out.value if st == TG_OK else None)
+
+
+def tg_graph_destroy(ctx, g):
+    return load().tg_graph_destroy(_vp(ctx), _vp(g))
+
+
+def tg_graph_get_info(g) -> dict:
+    info = tg_graph_info()
+    _check(load().tg_graph_get_info(_vp(g), ctypes.byref(info)), "tg_graph_get_info")
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def tg_run(ctx, g) -> int:
+    return load().tg_run(_vp(ctx), _vp(g))
+
+
+def tg_submit(ctx, g):
+    t = _u64(0)
+    st = load().tg_submit(_vp(ctx), _vp(g), ctypes.byref(t))
+    return st, t.value
+
+
+def tg_poll(ctx, ticket) -> int:
+    return load().tg_poll(_vp(ctx), ticket)
+
+
+def tg_wait(ctx, ticket) -> int:
+    return load().tg_wait(_vp(ctx), ticket)
+
+
+def tg_cancel(ctx) -> int:
+    return load().tg_cancel(_vp(ctx))
+
+
+def tg_result_copy(ctx, g, n):
+    out = np.empty(n, np.uint32)
+    cnt = np.empty(n, np.uint32)
+    dig = np.empty(n, np.uint32)
+    tot = _u64(0)
+    _check(load().tg_result_copy(_vp(ctx), _vp(g), out.ctypes.data_as(_vp), cnt.ctypes.data_as(_vp),
+                                 dig.ctypes.data_as(_vp), ctypes.byref(tot)), "tg_result_copy")
+    return out, cnt, dig, tot.value
+
+
+def _handles(gs):
+    arr = (_vp * len(gs))(*[_vp(g) for g in gs])
+    return arr
+
+
+def tg_batch_create(ctx, gs):
+    out = _vp()
+    st = load().tg_batch_create(_vp(ctx), ctypes.cast(_handles(gs), _vp), len(gs), ctypes.byref(out))
+    return st, (out.value if st == TG_OK else None)
+
+
+def tg_batch_launch(ctx, b) -> int:
+    return load().tg_batch_launch(_vp(ctx), _vp(b))
+
+
+def tg_batch_wait(ctx, b, n):
+    sts = np.zeros(n, np.int32)
+    st = load().tg_batch_wait(_vp(ctx), _vp(b), sts.ctypes.data_as(_vp))
+    return st, sts
+
+
+def tg_batch_destroy(ctx, b) -> int:
+    return load().tg_batch_destroy(_vp(ctx), _vp(b))
+
+
+def tg_run_batch(ctx, gs):
+    sts = np.zeros(len(gs), np.int32)
+    st = load().tg_run_batch(_vp(ctx), ctypes.cast(_handles(gs), _vp), len(gs), sts.ctypes.data_as(_vp))
+    return st, sts
+
+
+def tg_ctx_get_stats(ctx) -> dict:
+    s = tg_stats()
+    _check(load().tg_ctx_get_stats(_vp(ctx), ctypes.byref(s)), "tg_ctx_get_stats")
+    return s.as_dict()
+
+
+def tg_ctx_get_opts(ctx) -> dict:
+    o = tg_ctx_opts()
+    _check(load().tg_ctx_get_opts(_vp(ctx), ctypes.byref(o)), "tg_ctx_get_opts")
+    return {k: getattr(o, k) for k, _ in o._fields_}
+
+
+def tg_bench_payload(ctx, count, rounds):
+    ns = _u64(0)
+    cs = _u32(0)
+    _check(load().tg_bench_payload(_vp(ctx), count, rounds, ctypes.byref(ns), ctypes.byref(cs)), "tg_bench_payload")
+    return ns.value, cs.value
+
+
+def tg_bench_atomics(ctx, count, footprint_words):
+    ns = _u64(0)
+    _check(load().tg_bench_atomics(_vp(ctx), count, footprint_words, ctypes.byref(ns)), "tg_bench_atomics")
+    return ns.value

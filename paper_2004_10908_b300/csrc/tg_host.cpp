@@ -1,0 +1,965 @@
+// tg_host.cpp -- host side of libtg: context and arena pools, graph ingest /
+// validation / CSR packing (strong/weak rule of "Scheduling Condition Tasks",
+// source set of Algorithm 8), launches, batches and tickets.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/tg.h"
+#include "tg_internal.h"
+
+using namespace tg;
+
+namespace {
+
+constexpr u32 kMaxGraphs = 1u << 16;
+constexpr u32 kMaxDegree = 0xFFFFu;
+
+u64 now_ns()
+{
+    return (u64)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+u64 next_pow2(u64 x)
+{
+    u64 p = 1;
+    while (p < x)
+        p <<= 1;
+    return p;
+}
+
+bool is_pow2(u64 x) { return x && !(x & (x - 1)); }
+
+// First-fit range allocator over [0, cap).
+struct RangeAlloc {
+    std::map<u64, u64> free_;   // start -> length
+    u64 cap = 0;
+
+    void init(u64 c)
+    {
+        cap = c;
+        free_.clear();
+        if (c)
+            free_[0] = c;
+    }
+    bool alloc(u64 n, u64 &off)
+    {
+        if (n == 0) {
+            off = 0;
+            return true;
+        }
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                off = it->first;
+                u64 rest = it->second - n;
+                free_.erase(it);
+                if (rest)
+                    free_[off + n] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(u64 off, u64 n)
+    {
+        if (n == 0)
+            return;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+}  // namespace
+
+struct tg_graph {
+    tg_ctx *ctx = nullptr;
+    u32 gid = 0;
+    u32 n = 0, m = 0, n_src = 0, n_cond = 0;
+    u64 node_off = 0, edge_off = 0, edge_len = 0;
+    u32 seed = 0;
+    u64 pack_ns = 0, upload_ns = 0, bytes = 0;
+    cudaEvent_t busy = nullptr;   // event of the launch it is in (null: idle)
+};
+
+struct tg_batch {
+    tg_ctx *ctx = nullptr;
+    std::vector<tg_graph *> gs;
+    u64 lt_off = 0, lt_len = 0;
+    KParams kp{};
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    bool launched = false;
+};
+
+struct Submission {
+    tg_graph *g = nullptr;
+    cudaEvent_t ev = nullptr;
+    int status = TG_PENDING;
+};
+
+struct tg_ctx {
+    int device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    tg_ctx_opts opts{};
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+
+    LaunchCtl *ctl = nullptr;
+    u64 *stats = nullptr;
+    GDesc *descs = nullptr;
+    QCtr *dqc = nullptr;
+    u64 *dq = nullptr;
+    u64 *inj = nullptr;
+    u32 *scratch = nullptr;
+    u32 *thief_slots = nullptr;
+    NodeSlot *slots = nullptr;
+    u32 *outv = nullptr;
+    u32 *gidv = nullptr;
+    u32 *edges = nullptr;
+
+    u64 node_cap = 0, edge_cap = 0, inj_cap = 0;
+    RangeAlloc nodes, edge_pool;
+    std::vector<u32> free_gids;
+    u64 budget = 0, used = 0;
+
+    int nblocks = 0, threads = 0;
+    u32 smem_entries = 0, dq_depth = 0;
+
+    u32 *h_cancel = nullptr, *d_cancel = nullptr;
+    i32 *h_status = nullptr, *d_status = nullptr;
+    char *h_stage = nullptr;
+    size_t stage_bytes = 0;
+
+    bool dirty = true;   // queue slots may hold stale entries: clear before the next launch
+    u64 next_ticket = 1;
+    std::map<u64, Submission> subs;
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
+    bool timed = false;
+};
+
+namespace {
+
+#define TG_CUDA(call)                       \
+    do {                                    \
+        cudaError_t e_ = (call);            \
+        if (e_ != cudaSuccess)              \
+            return TG_ERR_CUDA;             \
+    } while (0)
+
+KParams base_params(tg_ctx *c)
+{
+    KParams p{};
+    p.slots = c->slots;
+    p.outv = c->outv;
+    p.gidv = c->gidv;
+    p.edges = c->edges;
+    p.descs = c->descs;
+    p.ctl = c->ctl;
+    p.stats = c->stats;
+    p.inj = c->inj;
+    p.inj_mask = (u32)(c->inj_cap - 1);
+    p.nblocks = (u32)c->nblocks;
+    p.dq = c->dq;
+    p.dqc = c->dqc;
+    p.dq_mask = c->dq_depth - 1u;
+    p.smem_mask = c->smem_entries - 1u;
+    p.flags = c->opts.flags;
+    p.max_steal = (u32)c->opts.max_steal;
+    p.steal_policy = (u32)c->opts.steal_policy;
+    p.node_cap = (u32)c->node_cap;
+    p.idle_sleep_ns = c->opts.idle_sleep_ns;
+    p.max_thieves = (u32)c->opts.max_thieves;
+    p.thief_slots = c->thief_slots;
+    p.time_limit_ns = c->opts.time_limit_ns;
+    p.cancel = c->d_cancel;
+    p.status_out = c->d_status;
+    return p;
+}
+
+int ensure_stage(tg_ctx *c, size_t bytes)
+{
+    if (c->stage_bytes >= bytes)
+        return TG_OK;
+    if (c->h_stage) {
+        cudaStreamSynchronize(c->stream);
+        cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->stage_bytes = 0;
+    }
+    size_t want = std::max(bytes, (size_t)1 << 22);
+    if (cudaHostAlloc((void **)&c->h_stage, want, cudaHostAllocDefault) != cudaSuccess)
+        return TG_ERR_CUDA;
+    c->stage_bytes = want;
+    return TG_OK;
+}
+
+// A graph is busy while the event of its last launch has not completed.
+bool graph_busy(tg_graph *g)
+{
+    if (!g->busy)
+        return false;
+    if (cudaEventQuery(g->busy) == cudaErrorNotReady)
+        return true;
+    g->busy = nullptr;
+    return false;
+}
+
+void note_status(tg_ctx *c, int st)
+{
+    if (st == TG_ERR_TIMEOUT || st == TG_ERR_CANCELLED || st == TG_ERR_INTERNAL)
+        c->dirty = true;
+}
+
+int clear_if_dirty(tg_ctx *c)
+{
+    if (!c->dirty)
+        return TG_OK;
+    TG_CUDA(launch_clear(c->inj, c->inj_cap, c->stream));
+    TG_CUDA(launch_clear(c->dq, (size_t)c->nblocks * c->dq_depth, c->stream));
+    c->dirty = false;
+    return TG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tg_strerror(int s)
+{
+    switch (s) {
+    case TG_OK: return "ok";
+    case TG_PENDING: return "pending";
+    case TG_ERR_INVALID: return "invalid argument or graph";
+    case TG_ERR_NO_SOURCE: return "no task with zero strong and zero weak in-edges";
+    case TG_ERR_EDGE_KIND: return "explicit edge kind disagrees with the source task's kind";
+    case TG_ERR_BUDGET: return "graph does not fit the memory budget";
+    case TG_ERR_RACE: return "task race: activation of a task already queued or running";
+    case TG_ERR_EXEC_LIMIT: return "execution cap exceeded";
+    case TG_ERR_TIMEOUT: return "device time limit expired";
+    case TG_ERR_CANCELLED: return "cancelled";
+    case TG_ERR_CUDA: return "CUDA runtime error";
+    case TG_ERR_INTERNAL: return "scheduler internal error (bounded wait gave up)";
+    case TG_ERR_BUSY: return "graph already in flight";
+    default: return "unknown status";
+    }
+}
+
+int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const tg_ctx_opts *opts,
+                  tg_ctx **out)
+{
+    if (!out || !dev_arena || ((uintptr_t)dev_arena & 255u) != 0)
+        return TG_ERR_INVALID;
+    *out = nullptr;
+    tg_ctx *c = new (std::nothrow) tg_ctx();
+    if (!c)
+        return TG_ERR_INVALID;
+    if (opts)
+        c->opts = *opts;
+    tg_ctx_opts &o = c->opts;
+    if (o.warps_per_block <= 0)
+        o.warps_per_block = 8;
+    if (o.warps_per_block > 32) {
+        delete c;
+        return TG_ERR_INVALID;
+    }
+    if (o.deque_depth <= 0)
+        o.deque_depth = 4096;
+    if (o.smem_ring <= 0)
+        o.smem_ring = 1024;
+    if (!is_pow2((u64)o.deque_depth) || !is_pow2((u64)o.smem_ring) || o.smem_ring < 64 || o.deque_depth < 64) {
+        delete c;
+        return TG_ERR_INVALID;
+    }
+    if (o.max_steal <= 0)
+        o.max_steal = 8;
+    if (o.idle_sleep_ns == 0)
+        o.idle_sleep_ns = 256;
+    if (o.max_thieves <= 0)
+        o.max_thieves = 16;
+    if (o.max_thieves > 1024) {
+        delete c;
+        return TG_ERR_INVALID;
+    }
+    if (o.steal_policy < 0 || o.steal_policy > 1) {
+        delete c;
+        return TG_ERR_INVALID;
+    }
+    if (o.time_limit_ns == 0)
+        o.time_limit_ns = 10ull * 1000 * 1000 * 1000;
+    if (o.exec_cap == 0 || o.exec_cap > (1ull << 31))
+        o.exec_cap = 1ull << 31;
+
+    c->stream = (cudaStream_t)cuda_stream;
+    c->arena = (char *)dev_arena;
+    c->arena_bytes = arena_bytes;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        delete c;
+        return TG_ERR_CUDA;
+    }
+    c->threads = o.warps_per_block * 32;
+    c->smem_entries = (u32)o.smem_ring;
+    c->dq_depth = (u32)o.deque_depth;
+    int per_sm = 0;
+    if (sched_occupancy(c->threads, sched_dyn_smem(c->smem_entries, (u32)o.warps_per_block), &per_sm) != cudaSuccess || per_sm <= 0) {
+        delete c;
+        return TG_ERR_CUDA;
+    }
+    int max_blocks = per_sm * c->sm_count;
+    c->nblocks = o.worker_blocks > 0 ? std::min(o.worker_blocks, max_blocks) : max_blocks;
+    o.worker_blocks = c->nblocks;
+
+    // ---- carve the arena
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        off = (off + 255) & ~(size_t)255;
+        char *p = c->arena + off;
+        off += bytes;
+        return p;
+    };
+    c->ctl = (LaunchCtl *)take(sizeof(LaunchCtl));
+    c->stats = (u64 *)take((size_t)c->nblocks * ST_COUNT * sizeof(u64));
+    c->scratch = (u32 *)take(4096);
+    c->thief_slots = (u32 *)take((size_t)1024 * 128);
+    c->descs = (GDesc *)take((size_t)kMaxGraphs * sizeof(GDesc));
+    c->dqc = (QCtr *)take((size_t)c->nblocks * sizeof(QCtr));
+    c->dq = (u64 *)take((size_t)c->nblocks * c->dq_depth * sizeof(u64));
+    off = (off + 255) & ~(size_t)255;
+    if (off >= arena_bytes) {
+        delete c;
+        return TG_ERR_INVALID;
+    }
+    size_t rest = arena_bytes - off - 4096;
+    u64 ncap = o.max_nodes, ecap = o.max_edges;
+    if (ncap == 0) {
+        ncap = (rest / 96) & ~(u64)255;
+        if (ncap > kMaxNodeIndex)
+            ncap = kMaxNodeIndex & ~(u64)255;
+    }
+    if (ncap == 0 || ncap > kMaxNodeIndex) {
+        delete c;
+        return TG_ERR_INVALID;
+    }
+    u64 icap = next_pow2(ncap + 4096);
+    size_t fixed = (size_t)ncap * (sizeof(NodeSlot) + 8) + (size_t)icap * 8 + 1024;
+    if (fixed >= rest) {
+        delete c;
+        return TG_ERR_INVALID;
+    }
+    if (ecap == 0)
+        ecap = std::min<u64>((rest - fixed) / 4, 0xFFFFFFF0ull);
+    if ((size_t)ecap * 4 + fixed > rest || ecap == 0) {
+        delete c;
+        return TG_ERR_INVALID;
+    }
+    c->inj = (u64 *)take((size_t)icap * 8);
+    c->slots = (NodeSlot *)take((size_t)ncap * sizeof(NodeSlot));
+    c->outv = (u32 *)take((size_t)ncap * 4);
+    c->gidv = (u32 *)take((size_t)ncap * 4);
+    c->edges = (u32 *)take((size_t)ecap * 4);
+    if (off > arena_bytes) {
+        delete c;
+        return TG_ERR_INVALID;
+    }
+    c->node_cap = ncap;
+    c->edge_cap = ecap;
+    c->inj_cap = icap;
+    c->nodes.init(ncap);
+    c->edge_pool.init(ecap);
+    c->budget = o.mem_budget_bytes ? o.mem_budget_bytes : (u64)ncap * 40 + (u64)ecap * 4;
+    c->free_gids.reserve(kMaxGraphs);
+    for (u32 g = kMaxGraphs; g-- > 0;)
+        c->free_gids.push_back(g);
+
+    if (cudaHostAlloc((void **)&c->h_cancel, 64, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->d_cancel, c->h_cancel, 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_status, kMaxGraphs * sizeof(i32), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->d_status, c->h_status, 0) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&c->ev_k0) != cudaSuccess || cudaEventCreate(&c->ev_k1) != cudaSuccess) {
+        tg_ctx_destroy(c);
+        return TG_ERR_CUDA;
+    }
+    *(volatile u32 *)c->h_cancel = 0;
+    memset(c->h_status, 0, kMaxGraphs * sizeof(i32));
+    if (cudaMemsetAsync(c->ctl, 0, sizeof(LaunchCtl), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->descs, 0, (size_t)kMaxGraphs * sizeof(GDesc), c->stream) != cudaSuccess) {
+        tg_ctx_destroy(c);
+        return TG_ERR_CUDA;
+    }
+    c->dirty = true;
+    if (clear_if_dirty(c) != TG_OK || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        tg_ctx_destroy(c);
+        return TG_ERR_CUDA;
+    }
+    *out = c;
+    return TG_OK;
+}
+
+int tg_ctx_destroy(tg_ctx *c)
+{
+    if (!c)
+        return TG_ERR_INVALID;
+    cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->subs)
+        if (kv.second.ev)
+            cudaEventDestroy(kv.second.ev);
+    if (c->h_cancel)
+        cudaFreeHost(c->h_cancel);
+    if (c->h_status)
+        cudaFreeHost(c->h_status);
+    if (c->h_stage)
+        cudaFreeHost(c->h_stage);
+    if (c->capture_stream)
+        cudaStreamDestroy(c->capture_stream);
+    if (c->ev_k0)
+        cudaEventDestroy(c->ev_k0);
+    if (c->ev_k1)
+        cudaEventDestroy(c->ev_k1);
+    delete c;
+    return TG_OK;
+}
+
+int tg_ctx_get_opts(const tg_ctx *c, tg_ctx_opts *o)
+{
+    if (!c || !o)
+        return TG_ERR_INVALID;
+    *o = c->opts;
+    o->max_nodes = c->node_cap;
+    o->max_edges = c->edge_cap;
+    o->mem_budget_bytes = c->budget;
+    return TG_OK;
+}
+
+int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t *params, uint32_t m,
+                    const uint32_t *src, const uint32_t *dst, const uint8_t *weak, uint32_t seed, tg_graph **out)
+{
+    if (!c || !out || n == 0 || !kinds || !params || (m && (!src || !dst)))
+        return TG_ERR_INVALID;
+    *out = nullptr;
+    const u64 t0 = now_ns();
+    // ---- validation (same order as the rule statement in tg.h)
+    u32 n_cond = 0;
+    for (u32 v = 0; v < n; ++v) {
+        if (kinds[v] > TG_COND_CONST)
+            return TG_ERR_INVALID;
+        if (kinds[v] == TG_COND_LOOP && ((params[v] >> 16) & 0xFFu) == 0u)
+            return TG_ERR_INVALID;
+        n_cond += kinds[v] != TG_STATIC;
+    }
+    for (u32 e = 0; e < m; ++e)
+        if (src[e] >= n || dst[e] >= n)
+            return TG_ERR_INVALID;
+    std::vector<u32> outdeg(n, 0), sin(n, 0), win(n, 0);
+    for (u32 e = 0; e < m; ++e) {
+        outdeg[src[e]]++;
+        if (kinds[src[e]] == TG_STATIC)
+            sin[dst[e]]++;
+        else
+            win[dst[e]]++;
+    }
+    for (u32 v = 0; v < n; ++v) {
+        if (kinds[v] != TG_STATIC && outdeg[v] == 0)
+            return TG_ERR_INVALID;
+        if (outdeg[v] > kMaxDegree || sin[v] > kMaxDegree)
+            return TG_ERR_INVALID;
+    }
+    if (weak)
+        for (u32 e = 0; e < m; ++e)
+            if ((weak[e] != 0) != (kinds[src[e]] != TG_STATIC))
+                return TG_ERR_EDGE_KIND;
+    u32 n_src = 0;
+    for (u32 v = 0; v < n; ++v)
+        n_src += (sin[v] == 0 && win[v] == 0);
+    if (n_src == 0)
+        return TG_ERR_NO_SOURCE;
+
+    // ---- pool space
+    const u64 bytes = (u64)n * 40 + ((u64)m + n_src) * 4;
+    if (c->used + bytes > c->budget || c->free_gids.empty())
+        return TG_ERR_BUDGET;
+    tg_graph *g = new (std::nothrow) tg_graph();
+    if (!g)
+        return TG_ERR_INVALID;
+    if (!c->nodes.alloc(n, g->node_off)) {
+        delete g;
+        return TG_ERR_BUDGET;
+    }
+    g->edge_len = (u64)m + n_src;
+    if (!c->edge_pool.alloc(g->edge_len, g->edge_off)) {
+        c->nodes.release(g->node_off, n);
+        delete g;
+        return TG_ERR_BUDGET;
+    }
+    g->gid = c->free_gids.back();
+    c->free_gids.pop_back();
+    c->used += bytes;
+    g->ctx = c;
+    g->n = n;
+    g->m = m;
+    g->n_src = n_src;
+    g->n_cond = n_cond;
+    g->seed = seed;
+    g->bytes = bytes;
+
+    // ---- pack: 32-byte node records, successors in insertion order, sources
+    const size_t slot_bytes = (size_t)n * sizeof(NodeSlot);
+    const size_t gid_bytes = (size_t)n * 4;
+    const size_t edge_bytes = (size_t)g->edge_len * 4;
+    int rc = ensure_stage(c, slot_bytes + gid_bytes + edge_bytes + 256);
+    if (rc != TG_OK) {
+        tg_graph_destroy(c, g);
+        return rc;
+    }
+    cudaStreamSynchronize(c->stream);   // staging buffer may still feed an earlier copy
+    NodeSlot *hs = (NodeSlot *)c->h_stage;
+    u32 *hg = (u32 *)(c->h_stage + slot_bytes);
+    u32 *he = (u32 *)(c->h_stage + slot_bytes + gid_bytes);
+    const u32 node_base = (u32)g->node_off;
+    const u32 edge_base = (u32)g->edge_off;
+    u32 acc = 0;
+    for (u32 v = 0; v < n; ++v) {
+        NodeSlot &s = hs[v];
+        const u32 kind = kinds[v];
+        u32 arg = 0;
+        if (kind == TG_COND_LOOP)
+            arg = (params[v] >> 16) & 0xFFu;
+        else if (kind == TG_COND_CONST)
+            arg = params[v] >> 24;
+        s.succ_off = edge_base + acc;
+        s.deg = outdeg[v] | (sin[v] << 16);
+        s.prm = (params[v] & 0xFFFFu) | (kind << 16) | (arg << 24);
+        s.lid = v;
+        s.W = sin[v];
+        s.cnt = 0;
+        s.dig = 0;
+        hg[v] = g->gid;
+        outdeg[v] = acc;   // reuse as the fill cursor
+        acc += (u32)(s.deg & 0xFFFFu);
+    }
+    for (u32 e = 0; e < m; ++e)
+        he[outdeg[src[e]]++] = node_base + dst[e];
+    for (u32 v = 0, k = 0; v < n; ++v)
+        if (sin[v] == 0 && win[v] == 0)
+            he[m + k++] = node_base + v;
+    const u64 t1 = now_ns();
+
+    GDesc d{};
+    d.pe = 0;
+    d.status = 0;
+    d.seed = seed;
+    d.node_off = node_base;
+    d.n = n;
+    d.src_off = edge_base + m;
+    d.n_src = n_src;
+    d.exec_cap = (u32)std::min<u64>(c->opts.exec_cap, 0xFFFFFFFFull);
+    static_assert(sizeof(GDesc) <= 256, "stage tail");
+    memcpy(c->h_stage + slot_bytes + gid_bytes + edge_bytes, &d, sizeof(d));
+    cudaError_t e1 = cudaMemcpyAsync(c->slots + g->node_off, hs, slot_bytes, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e2 = cudaMemcpyAsync(c->gidv + g->node_off, hg, gid_bytes, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e3 = cudaMemcpyAsync(c->edges + g->edge_off, he, edge_bytes, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e4 = cudaMemcpyAsync(c->descs + g->gid, c->h_stage + slot_bytes + gid_bytes + edge_bytes,
+                                     sizeof(GDesc), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e5 = cudaStreamSynchronize(c->stream);
+    if (e1 || e2 || e3 || e4 || e5) {
+        tg_graph_destroy(c, g);
+        return TG_ERR_CUDA;
+    }
+    g->pack_ns = t1 - t0;
+    g->upload_ns = now_ns() - t1;
+    *out = g;
+    return TG_OK;
+}
+
+int tg_graph_destroy(tg_ctx *c, tg_graph *g)
+{
+    if (!c || !g || g->ctx != c)
+        return TG_ERR_INVALID;
+    if (g->busy)
+        cudaEventSynchronize(g->busy);
+    c->nodes.release(g->node_off, g->n);
+    c->edge_pool.release(g->edge_off, g->edge_len);
+    c->free_gids.push_back(g->gid);
+    c->used -= g->bytes;
+    for (auto it = c->subs.begin(); it != c->subs.end();) {
+        if (it->second.g == g) {
+            if (it->second.ev)
+                cudaEventDestroy(it->second.ev);
+            it = c->subs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    delete g;
+    return TG_OK;
+}
+
+int tg_graph_get_info(const tg_graph *g, tg_graph_info *info)
+{
+    if (!g || !info)
+        return TG_ERR_INVALID;
+    info->n_nodes = g->n;
+    info->n_edges = g->m;
+    info->n_sources = g->n_src;
+    info->n_conditions = g->n_cond;
+    info->device_bytes = g->bytes;
+    info->pack_ns = g->pack_ns;
+    info->upload_ns = g->upload_ns;
+    return TG_OK;
+}
+
+int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
+{
+    if (!c || !g || g->ctx != c || !ticket)
+        return TG_ERR_INVALID;
+    if (graph_busy(g))
+        return TG_ERR_BUSY;
+    int rc = clear_if_dirty(c);
+    if (rc != TG_OK)
+        return rc;
+    KParams p = base_params(c);
+    p.lt = nullptr;
+    p.n_graphs = 1;
+    p.single_gid = g->gid;
+    p.max_n = g->n;
+    p.total_sources = g->n_src;
+    Submission s;
+    s.g = g;
+    TG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+    TG_CUDA(launch_rearm(p, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    TG_CUDA(launch_sched(p, c->nblocks, c->threads, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    TG_CUDA(launch_finalize(p, c->stream));
+    TG_CUDA(cudaEventRecord(s.ev, c->stream));
+    c->timed = true;
+    g->busy = s.ev;
+    *ticket = c->next_ticket++;
+    c->subs[*ticket] = s;
+    return TG_OK;
+}
+
+static int finish_sub(tg_ctx *c, Submission &s)
+{
+    if (s.status == TG_PENDING) {
+        s.status = c->h_status[s.g->gid];
+        note_status(c, s.status);
+        if (s.g->busy == s.ev)
+            s.g->busy = nullptr;
+    }
+    return s.status;
+}
+
+int tg_poll(tg_ctx *c, uint64_t ticket)
+{
+    if (!c)
+        return TG_ERR_INVALID;
+    auto it = c->subs.find(ticket);
+    if (it == c->subs.end())
+        return TG_ERR_INVALID;
+    Submission &s = it->second;
+    if (s.status != TG_PENDING)
+        return s.status;
+    cudaError_t q = cudaEventQuery(s.ev);
+    if (q == cudaErrorNotReady)
+        return TG_PENDING;
+    if (q != cudaSuccess)
+        return TG_ERR_CUDA;
+    return finish_sub(c, s);
+}
+
+int tg_wait(tg_ctx *c, uint64_t ticket)
+{
+    if (!c)
+        return TG_ERR_INVALID;
+    auto it = c->subs.find(ticket);
+    if (it == c->subs.end())
+        return TG_ERR_INVALID;
+    Submission &s = it->second;
+    if (s.status != TG_PENDING)
+        return s.status;
+    if (cudaEventSynchronize(s.ev) != cudaSuccess)
+        return TG_ERR_CUDA;
+    return finish_sub(c, s);
+}
+
+int tg_run(tg_ctx *c, tg_graph *g)
+{
+    uint64_t t = 0;
+    int rc = tg_submit(c, g, &t);
+    if (rc != TG_OK)
+        return rc;
+    rc = tg_wait(c, t);
+    auto it = c->subs.find(t);
+    if (it != c->subs.end()) {
+        cudaEventDestroy(it->second.ev);
+        c->subs.erase(it);
+    }
+    return rc;
+}
+
+int tg_cancel(tg_ctx *c)
+{
+    if (!c)
+        return TG_ERR_INVALID;
+    *(volatile u32 *)c->h_cancel = 1u;
+    return TG_OK;
+}
+
+int tg_result_copy(tg_ctx *c, const tg_graph *g, uint32_t *out, uint32_t *cnt, uint32_t *dig,
+                   uint64_t *total_execs)
+{
+    if (!c || !g || g->ctx != c)
+        return TG_ERR_INVALID;
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    if (out)
+        TG_CUDA(cudaMemcpy(out, c->outv + g->node_off, (size_t)g->n * 4, cudaMemcpyDeviceToHost));
+    if (cnt || dig || total_execs) {
+        std::vector<NodeSlot> tmp(g->n);
+        TG_CUDA(cudaMemcpy(tmp.data(), c->slots + g->node_off, (size_t)g->n * sizeof(NodeSlot),
+                           cudaMemcpyDeviceToHost));
+        u64 tot = 0;
+        for (u32 v = 0; v < g->n; ++v) {
+            const u32 k = tmp[v].cnt & ~kInflight;
+            if (cnt)
+                cnt[v] = k;
+            if (dig)
+                dig[v] = tmp[v].dig;
+            tot += k;
+        }
+        if (total_execs)
+            *total_execs = tot;
+    }
+    return TG_OK;
+}
+
+int tg_batch_create(tg_ctx *c, tg_graph *const *gs, uint32_t n, tg_batch **out)
+{
+    if (!c || !gs || !out || n == 0 || n > kMaxGraphs)
+        return TG_ERR_INVALID;
+    *out = nullptr;
+    std::vector<LEntry> lt(n);
+    u64 inj = 0;
+    u32 max_n = 0;
+    for (u32 i = 0; i < n; ++i) {
+        if (!gs[i] || gs[i]->ctx != c)
+            return TG_ERR_INVALID;
+        for (u32 j = 0; j < i; ++j)
+            if (gs[j] == gs[i])
+                return TG_ERR_INVALID;
+        lt[i].gid = gs[i]->gid;
+        lt[i].inj_base = (u32)inj;
+        inj += gs[i]->n_src;
+        max_n = std::max(max_n, gs[i]->n);
+    }
+    if (inj > c->inj_cap)
+        return TG_ERR_BUDGET;
+    tg_batch *b = new (std::nothrow) tg_batch();
+    if (!b)
+        return TG_ERR_INVALID;
+    b->ctx = c;
+    b->gs.assign(gs, gs + n);
+    b->lt_len = (u64)n * 2;
+    if (!c->edge_pool.alloc(b->lt_len, b->lt_off)) {
+        delete b;
+        return TG_ERR_BUDGET;
+    }
+    if (cudaMemcpy(c->edges + b->lt_off, lt.data(), (size_t)n * sizeof(LEntry), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+        tg_batch_destroy(c, b);
+        return TG_ERR_CUDA;
+    }
+    KParams p = base_params(c);
+    p.lt = (const LEntry *)(c->edges + b->lt_off);
+    p.n_graphs = n;
+    p.single_gid = 0;
+    p.max_n = max_n;
+    p.total_sources = (u32)inj;
+    b->kp = p;
+    // capture re-arm + scheduler + finalize once; replays reuse it
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cs = c->capture_stream;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        tg_batch_destroy(c, b);
+        return TG_ERR_CUDA;
+    }
+    cudaError_t e1 = launch_rearm(p, cs);
+    cudaError_t e2 = launch_sched(p, c->nblocks, c->threads, cs);
+    cudaError_t e3 = launch_finalize(p, cs);
+    cudaError_t e4 = cudaStreamEndCapture(cs, &graph);
+    if (e1 || e2 || e3 || e4 || !graph) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        tg_batch_destroy(c, b);
+        return TG_ERR_CUDA;
+    }
+    cudaError_t e5 = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e5 != cudaSuccess || cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+        tg_batch_destroy(c, b);
+        return TG_ERR_CUDA;
+    }
+    *out = b;
+    return TG_OK;
+}
+
+int tg_batch_launch(tg_ctx *c, tg_batch *b)
+{
+    if (!c || !b || b->ctx != c)
+        return TG_ERR_INVALID;
+    for (tg_graph *g : b->gs)
+        if (graph_busy(g))
+            return TG_ERR_BUSY;
+    int rc = clear_if_dirty(c);
+    if (rc != TG_OK)
+        return rc;
+    TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    TG_CUDA(cudaGraphLaunch(b->exec, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    TG_CUDA(cudaEventRecord(b->done, c->stream));
+    c->timed = true;
+    for (tg_graph *g : b->gs)
+        g->busy = b->done;
+    b->launched = true;
+    return TG_OK;
+}
+
+int tg_batch_wait(tg_ctx *c, tg_batch *b, int *statuses)
+{
+    if (!c || !b || b->ctx != c || !b->launched)
+        return TG_ERR_INVALID;
+    TG_CUDA(cudaEventSynchronize(b->done));
+    int first = TG_OK;
+    for (size_t i = 0; i < b->gs.size(); ++i) {
+        tg_graph *g = b->gs[i];
+        int st = c->h_status[g->gid];
+        note_status(c, st);
+        if (statuses)
+            statuses[i] = st;
+        if (st != TG_OK && first == TG_OK)
+            first = st;
+        if (g->busy == b->done)
+            g->busy = nullptr;
+    }
+    b->launched = false;
+    return first;
+}
+
+int tg_batch_destroy(tg_ctx *c, tg_batch *b)
+{
+    if (!c || !b || b->ctx != c)
+        return TG_ERR_INVALID;
+    if (b->launched)
+        cudaEventSynchronize(b->done);
+    for (tg_graph *g : b->gs)
+        if (g->busy == b->done)
+            g->busy = nullptr;
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    if (b->done)
+        cudaEventDestroy(b->done);
+    if (b->lt_len)
+        c->edge_pool.release(b->lt_off, b->lt_len);
+    delete b;
+    return TG_OK;
+}
+
+int tg_run_batch(tg_ctx *c, tg_graph *const *gs, uint32_t n, int *statuses)
+{
+    tg_batch *b = nullptr;
+    int rc = tg_batch_create(c, gs, n, &b);
+    if (rc != TG_OK)
+        return rc;
+    rc = tg_batch_launch(c, b);
+    if (rc == TG_OK)
+        rc = tg_batch_wait(c, b, statuses);
+    tg_batch_destroy(c, b);
+    return rc;
+}
+
+int tg_ctx_get_stats(tg_ctx *c, tg_stats *st)
+{
+    if (!c || !st)
+        return TG_ERR_INVALID;
+    memset(st, 0, sizeof(*st));
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<u64> h((size_t)c->nblocks * ST_COUNT);
+    TG_CUDA(cudaMemcpy(h.data(), c->stats, h.size() * sizeof(u64), cudaMemcpyDeviceToHost));
+    for (int b = 0; b < c->nblocks; ++b) {
+        const u64 *s = &h[(size_t)b * ST_COUNT];
+        st->tasks += s[ST_TASKS];
+        st->pops_local += s[ST_POP_LOCAL];
+        st->pops_own += s[ST_POP_OWN];
+        st->steal_attempts += s[ST_STEAL_TRY];
+        st->steal_hits += s[ST_STEAL_HIT];
+        st->inject_pops += s[ST_INJECT];
+        st->spills += s[ST_SPILL];
+        st->idle_loops += s[ST_IDLE];
+        st->warp_iters += s[ST_ITERS];
+    }
+    if (c->timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1) == cudaSuccess)
+            st->kernel_ns = (u64)((double)ms * 1e6);
+    }
+    st->worker_blocks = (u32)c->nblocks;
+    st->warps_per_block = (u32)c->opts.warps_per_block;
+    return TG_OK;
+}
+
+int tg_bench_payload(tg_ctx *c, uint64_t count, uint32_t rounds, uint64_t *ns, uint32_t *checksum)
+{
+    if (!c || !ns)
+        return TG_ERR_INVALID;
+    TG_CUDA(cudaMemsetAsync(c->scratch, 0, 4, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    TG_CUDA(launch_bench_payload(count, rounds, c->scratch, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    u32 cs = 0;
+    TG_CUDA(cudaMemcpyAsync(&cs, c->scratch, 4, cudaMemcpyDeviceToHost, c->stream));
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    TG_CUDA(cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1));
+    *ns = (u64)((double)ms * 1e6);
+    if (checksum)
+        *checksum = cs;
+    c->timed = false;
+    return TG_OK;
+}
+
+int tg_bench_atomics(tg_ctx *c, uint64_t count, uint64_t footprint_words, uint64_t *ns)
+{
+    if (!c || !ns || footprint_words == 0 || footprint_words > c->inj_cap)
+        return TG_ERR_INVALID;
+    // the injection queue's memory serves as the footprint; it is cleared
+    // before the next scheduler launch
+    c->dirty = true;
+    TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    TG_CUDA(launch_bench_atomics(c->inj, footprint_words, count, (u64 *)c->scratch, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    TG_CUDA(cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1));
+    *ns = (u64)((double)ms * 1e6);
+    c->timed = false;
+    return TG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// tg_internal.h -- device data layout shared by the host library (tg_host.cpp)
+// and the kernels (tg_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tg {
+
+using u8 = uint8_t;
+using u32 = uint32_t;
+using i32 = int32_t;
+using u64 = unsigned long long;
+
+// One task of a resident graph: 32 bytes = one L2 sector, so the immutable
+// record and the mutable join/execution state arrive in a single read.
+struct alignas(32) NodeSlot {
+    u32 succ_off;   // first successor in the edge pool (global index)
+    u32 deg;        // successor count (bits 0-15) | strong in-degree (bits 16-31)
+    u32 prm;        // rounds (0-15) | kind (16-23) | arg (24-31): loop trip or constant index
+    u32 lid;        // the task's id inside its graph (payload input)
+    u64 W;          // join word: insum of the current round (hi 32) | remaining strong deps (lo 32)
+    u32 cnt;        // executions so far (bits 0-30) | in-flight flag (bit 31)
+    u32 dig;        // digest of all outputs
+};
+static_assert(sizeof(NodeSlot) == 32, "NodeSlot must be one sector");
+
+// Per-graph descriptor (indexed by graph slot id "gid").
+struct alignas(64) GDesc {
+    u64 pe;         // executions (hi 32) | pending activations (lo 32)
+    i32 status;     // 0 while running / ok, else TG_ERR_*
+    u32 seed;       // condition-hash seed
+    u32 node_off;   // first node slot
+    u32 n;          // tasks
+    u32 src_off;    // source list in the edge pool
+    u32 n_src;
+    u32 exec_cap;
+    u32 pad[7];
+};
+static_assert(sizeof(GDesc) == 64, "GDesc is 64 bytes");
+
+// One graph of a launch: its slot id and where its sources start in the
+// injection queue.
+struct LEntry {
+    u32 gid;
+    u32 inj_base;
+};
+
+// Head / tail of a multi-producer multi-consumer ring, on separate lines.
+struct alignas(128) QCtr {
+    u32 head;
+    u32 pad0[31];
+    u32 tail;
+    u32 pad1[31];
+};
+
+// Launch-wide control words (each on its own 128-byte line).
+struct alignas(128) LaunchCtl {
+    u32 graphs_left;
+    u32 pad0[31];
+    i32 abort_code;
+    u32 pad1[31];
+    u32 hungry;
+    u32 pad2[31];
+    QCtr inj;
+};
+
+enum StatIdx {
+    ST_TASKS = 0, ST_POP_LOCAL, ST_POP_OWN, ST_STEAL_TRY, ST_STEAL_HIT, ST_INJECT,
+    ST_SPILL, ST_IDLE, ST_ITERS, ST_COUNT = 16
+};
+
+constexpr u32 kEmpty32 = 0xFFFFFFFFu;
+constexpr u64 kEmpty = 0xFFFFFFFFFFFFFFFFull;
+constexpr u32 kStrongBit = 0x80000000u;   // in a ready entry's low word
+constexpr u32 kInflight = 0x80000000u;    // in NodeSlot::cnt
+constexpr u32 kMaxNodeIndex = 0x7FFFFFFEu;
+
+struct KParams {
+    NodeSlot *slots;
+    u32 *outv;
+    const u32 *gidv;
+    const u32 *edges;
+    GDesc *descs;
+    const LEntry *lt;      // launch table (nullptr: single graph `single_gid`)
+    u32 n_graphs;
+    u32 single_gid;
+    u32 max_n;             // largest graph of the launch (re-arm grid)
+    u32 total_sources;
+    LaunchCtl *ctl;
+    u64 *stats;            // [worker_blocks][ST_COUNT]
+    u64 *inj;              // injection queue slots
+    u32 inj_mask;
+    u32 nblocks;
+    u64 *dq;               // per-block public deques, nblocks x (dq_mask+1)
+    QCtr *dqc;
+    u32 dq_mask;
+    u32 smem_mask;
+    u32 flags;
+    u32 max_steal;
+    u32 steal_policy;
+    u32 node_cap;          // node pool size: a popped entry beyond it is a scheduler fault
+    u32 idle_sleep_ns;     // wait of a non-thief idle warp
+    u32 max_thieves;       // thief slots (blocks stealing / polling at once)
+    u32 *thief_slots;      // max_thieves words, each on its own 128-byte line
+    u64 time_limit_ns;
+    volatile u32 *cancel;  // host-mapped cancel flag (may be null)
+    i32 *status_out;       // host-mapped per-gid statuses (may be null)
+};
+
+// Launch helpers implemented in tg_kernels.cu (all enqueue on `st`).
+cudaError_t launch_rearm(const KParams &p, cudaStream_t st);
+cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_finalize(const KParams &p, cudaStream_t st);
+cudaError_t launch_clear(u64 *slots, size_t count, cudaStream_t st);
+cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm);
+size_t sched_dyn_smem(u32 smem_entries, u32 warps);
+cudaError_t launch_bench_payload(u64 count, u32 rounds, u32 *checksum, cudaStream_t st);
+cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink, cudaStream_t st);
+
+}  // namespace tg

@@ -1,0 +1,840 @@
+// tg_kernels.cu -- the device side of the task-graph executor (sm_103a).
+//
+// One persistent kernel runs every task of one or many graphs.  A worker is a
+// warp: it takes up to 32 ready activations at a time (one per lane), runs
+// their payloads, dispatches conditions (Algorithm 4: a condition submits
+// successors[r] and touches no join counter) and releases the strong
+// successors of static tasks with 64-bit atomics on their join words
+// (Algorithm 4: decrement, submit at zero).  Ready activations live in
+//   - a per-block ring in shared memory (the worker's local queue, Alg. 5),
+//   - a per-block public deque in global memory that other blocks steal
+//     from (Alg. 6/7: random victims, at most max_steal probes a round),
+//   - one shared injection queue that receives the sources (Alg. 8) and
+//     overflow.
+// All rings are multi-producer multi-consumer with monotonically increasing
+// 32-bit tickets and an EMPTY marker per slot; every wait is bounded.
+#include "tg_internal.h"
+#include "../../include/tg.h"
+
+namespace tg {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kSpinLimit = 1 << 20;     // bounded waits on a slot (iterations)
+constexpr int kCasTries = 256;
+constexpr u32 kStage = 256;             // staged activations per warp (shared memory)
+
+// ---------------------------------------------------------------------------
+// arithmetic of the method (payload, condition hash, digest)
+// ---------------------------------------------------------------------------
+// lowbias32 mixer (C. Wellons, 2018): xor-shift / odd-multiply steps.
+__device__ __forceinline__ u32 mix32(u32 x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+// Task payload: seed word from (id, iter, insum), then `rounds` x (add the
+// golden-ratio constant, mix).
+__device__ __forceinline__ u32 task_payload(u32 id, u32 iter, u32 insum, u32 rounds)
+{
+    u32 x = (id * 0x9E3779B9U) ^ (iter * 0x85EBCA6BU) ^ (insum * 0xC2B2AE35U) ^ 0x27D4EB2FU;
+#pragma unroll 4
+    for (u32 r = 0; r < rounds; ++r) {
+        x += 0x9E3779B9U;
+        x = mix32(x);
+    }
+    return x;
+}
+
+__device__ __forceinline__ u32 cond_hash(u32 seed, u32 id, u32 iter)
+{
+    return mix32(mix32(mix32(seed ^ 0xA511E9B3U) ^ id) ^ iter);
+}
+
+// Successor index returned by a condition task (may be out of range).
+__device__ __forceinline__ int cond_index(u32 kind, u32 arg, u32 seed, u32 id, u32 iter, u32 nsucc)
+{
+    if (kind == TG_COND_BRANCH)
+        return (int)(cond_hash(seed, id, iter) % nsucc);
+    if (kind == TG_COND_LOOP) {
+        if ((iter + 1u) % arg != 0u)
+            return 0;
+        if (nsucc <= 2u)
+            return 1;
+        return (int)(1u + cond_hash(seed, id, iter) % (nsucc - 1u));
+    }
+    return (int)(signed char)(unsigned char)arg;
+}
+
+// ---------------------------------------------------------------------------
+// memory helpers
+// ---------------------------------------------------------------------------
+// Relaxed loads/stores at GPU scope (generic addresses: global or shared).
+// C `volatile` would make them system-scope strong accesses, which take a
+// far slower path when thousands of warps poll.
+__device__ __forceinline__ u64 vld64(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void vst64(u64 *p, u64 v)
+{
+    asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ u32 vld32(const u32 *p)
+{
+    u32 v;
+    asm volatile("ld.relaxed.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ i32 vldi(const i32 *p) { return (i32)vld32((const u32 *)p); }
+__device__ __forceinline__ void vst32(u32 *p, u32 v)
+{
+    asm volatile("st.relaxed.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ u64 globaltimer()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ u32 lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+// Release/acquire fence at GPU scope: orders this thread's earlier writes
+// (outputs, state, flag releases) before its later publishing writes.  A
+// sequentially consistent fence is not needed and costs far more.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// multi-producer multi-consumer rings (shared or global memory)
+// ---------------------------------------------------------------------------
+struct Ring {
+    u32 *head;
+    u32 *tail;
+    u64 *slots;
+    u32 mask;
+};
+
+// Warp-cooperative pop into lanes [0, k).  A thief takes half of what it
+// sees (at least one); an owner takes up to 32.
+__device__ __forceinline__ int ring_pop(const Ring &r, bool thief, int lane, u64 &e, int &err)
+{
+    u32 h = 0;
+    int k = 0;
+    if (lane == 0) {
+        for (int t = 0; t < kCasTries; ++t) {
+            u32 hh = vld32(r.head), tt = vld32(r.tail);
+            int avail = (int)(tt - hh);
+            if (avail <= 0)
+                break;
+            int kk = thief ? min(32, (avail + 1) >> 1) : min(32, avail);
+            if (atomicCAS(r.head, hh, hh + (u32)kk) == hh) {
+                h = hh;
+                k = kk;
+                break;
+            }
+        }
+    }
+    k = __shfl_sync(kFull, k, 0);
+    h = __shfl_sync(kFull, h, 0);
+    e = kEmpty;
+    if (lane < k) {
+        u64 *s = r.slots + ((h + (u32)lane) & r.mask);
+        u64 v = vld64(s);
+        int spins = 0;
+        while ((u32)v == kEmpty32) {   // reserved by its producer, not yet written
+            if (++spins > kSpinLimit) {
+                err = 1;
+                break;
+            }
+            v = vld64(s);
+        }
+        if ((u32)v != kEmpty32)
+            vst64(s, kEmpty);
+        e = v;
+    }
+    return k;
+}
+
+// Warp-cooperative push of the lanes with `has`; all or nothing.
+__device__ __forceinline__ bool ring_push(const Ring &r, bool has, u64 ent, int lane, int &err)
+{
+    u32 m = __ballot_sync(kFull, has);
+    if (m == 0)
+        return true;
+    int k = __popc(m);
+    u32 t = 0;
+    int ok = 0;
+    if (lane == 0) {
+        for (int tr = 0; tr < kCasTries; ++tr) {
+            u32 tt = vld32(r.tail), hh = vld32(r.head);
+            if ((int)(tt + (u32)k - hh) > (int)(r.mask + 1u))
+                break;   // full
+            if (atomicCAS(r.tail, tt, tt + (u32)k) == tt) {
+                t = tt;
+                ok = 1;
+                break;
+            }
+        }
+    }
+    ok = __shfl_sync(kFull, ok, 0);
+    if (!ok)
+        return false;
+    t = __shfl_sync(kFull, t, 0);
+    if (has) {
+        u64 *s = r.slots + ((t + (u32)__popc(m & lanemask_lt(lane))) & r.mask);
+        int spins = 0;
+        while ((u32)vld64(s) != kEmpty32) {   // previous occupant not yet taken
+            if (++spins > kSpinLimit) {
+                err = 1;
+                break;
+            }
+        }
+        vst64(s, ent);
+    }
+    return true;
+}
+
+__device__ __forceinline__ u32 ring_size(const Ring &r) { return vld32(r.tail) - vld32(r.head); }
+
+// ---------------------------------------------------------------------------
+// the persistent scheduler
+// ---------------------------------------------------------------------------
+struct WarpCtx {
+    Ring local;      // block's shared-memory ring
+    Ring own;        // block's public deque
+    Ring inj;        // shared injection queue
+    u32 high_water;  // local ring size above which new work goes public
+    int err;
+};
+
+// Route the new ready activations of the warp (lanes with `has`).
+__device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u64 &spill_ctr)
+{
+    if (__ballot_sync(kFull, has) == 0)
+        return;
+    u32 lsz = 0;
+    if (lane == 0)
+        lsz = ring_size(w.local);
+    lsz = __shfl_sync(kFull, lsz, 0);
+    bool pub = has && lsz >= w.high_water;
+    bool loc = has && !pub;
+    if (!ring_push(w.local, loc, ent, lane, w.err))
+        pub = pub || loc;
+    if (__ballot_sync(kFull, pub) != 0) {
+        if (lane == 0)
+            spill_ctr++;
+        if (!ring_push(w.own, pub, ent, lane, w.err))
+            if (!ring_push(w.inj, pub, ent, lane, w.err))
+                w.err = 2;
+    }
+}
+
+// Stage the new activations of the lanes with `has` in the warp's buffer;
+// a full buffer is published early (its owners keep their flags meanwhile).
+__device__ __forceinline__ void stage(WarpCtx &w, u64 *buf, u32 &ns, bool has, u64 ent, int lane, u64 &spill_ctr)
+{
+    const u32 m = __ballot_sync(kFull, has);
+    if (m == 0)
+        return;
+    const u32 k = (u32)__popc(m);
+    if (ns + k > kStage) {
+        __syncwarp();
+        for (u32 i = 0; i < ns; i += 32u) {
+            const bool h = i + (u32)lane < ns;
+            emit(w, h, h ? buf[i + lane] : 0ull, lane, spill_ctr);
+        }
+        ns = 0;
+        __syncwarp();
+    }
+    if (has)
+        buf[ns + (u32)__popc(m & lanemask_lt(lane))] = ent;
+    ns += k;
+}
+
+__device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, u64 &spill_ctr)
+{
+    __syncwarp();
+    for (u32 i = 0; i < ns; i += 32u) {
+        const bool h = i + (u32)lane < ns;
+        emit(w, h, h ? buf[i + lane] : 0ull, lane, spill_ctr);
+    }
+}
+
+__global__ void sched_kernel(KParams p)
+{
+    extern __shared__ u64 s_ring[];
+    __shared__ u32 s_head, s_tail;
+    __shared__ u32 s_push[32 * 32];
+    __shared__ u32 s_keep[32 * 32];
+    __shared__ u64 s_stats[ST_COUNT];
+    __shared__ int s_thief, s_stop;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const u32 ring_n = p.smem_mask + 1u;
+    for (u32 i = threadIdx.x; i < ring_n; i += blockDim.x)
+        s_ring[i] = kEmpty;
+    if (threadIdx.x < ST_COUNT)
+        s_stats[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        s_head = 0;
+        s_tail = 0;
+        s_thief = 0;
+        s_stop = 0;
+    }
+    __syncthreads();
+
+    const bool race_check = (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
+    const u64 t0 = globaltimer();
+    const u64 deadline = t0 + p.time_limit_ns;
+
+    WarpCtx w;
+    w.local = Ring{&s_head, &s_tail, s_ring, p.smem_mask};
+    w.own = Ring{&p.dqc[blockIdx.x].head, &p.dqc[blockIdx.x].tail,
+                 p.dq + (size_t)blockIdx.x * (p.dq_mask + 1u), p.dq_mask};
+    w.inj = Ring{&p.ctl->inj.head, &p.ctl->inj.tail, p.inj, p.inj_mask};
+    // keep locally what the block's warps can take at once; beyond that,
+    // new activations go to the public deque where other blocks steal them
+    w.high_water = min(ring_n / 2u, max(64u, (blockDim.x / 32u) * 32u));
+    w.err = 0;
+    u32 *my_push = s_push + warp * 32;
+    u32 *my_keep = s_keep + warp * 32;
+    u64 *my_stage = s_ring + ring_n + (size_t)warp * kStage;
+
+    u64 st_tasks = 0, st_local = 0, st_own = 0, st_try = 0, st_hit = 0, st_inj = 0, st_spill = 0,
+        st_idle = 0, st_iters = 0;
+    u32 rng = mix32(blockIdx.x * 0x9E3779B9U + (u32)warp * 0x85EBCA6BU + 1u);
+    u32 backoff = 256;
+    const u32 my_slot = blockIdx.x % p.max_thieves;
+    u32 idle = 0;
+
+    for (;;) {
+        // ---- take work from the block's shared-memory ring
+        u64 e;
+        int k = ring_pop(w.local, false, lane, e, w.err);
+        if (k) {
+            st_local++;
+        } else {
+            // ---- idle.  One warp per block at a time is the block's thief
+            // (Alg. 6/7): it probes the own public deque, up to max_steal
+            // victims and the injection queue, and is the only warp of the
+            // block that polls launch-wide state.  The other idle warps wait
+            // on shared memory, so idle polling never floods L2.
+            if (*(volatile int *)&s_stop)
+                break;
+            int am = 0;
+            if (lane == 0) {
+                am = atomicCAS(&s_thief, 0, 1) == 0;
+                // at most max_thieves blocks steal / poll at once (the paper's
+                // bound on wasteful steals); slots live on separate lines
+                if (am && atomicCAS(&p.thief_slots[my_slot * 32u], 0u, 1u) != 0u) {
+                    *(volatile int *)&s_thief = 0;
+                    am = 2;
+                }
+            }
+            am = __shfl_sync(kFull, am, 0);
+            if (am != 1) {
+                st_idle++;
+                __nanosleep(am == 2 ? backoff : p.idle_sleep_ns);
+                if (am == 2)
+                    backoff = min(backoff * 2u, 4096u);
+                continue;
+            }
+            k = ring_pop(w.own, false, lane, e, w.err);
+            if (k) {
+                st_own++;
+            } else {
+                for (u32 a = 0; a < p.max_steal && k == 0 && p.nblocks > 1; ++a) {
+                    u32 v;
+                    if (p.steal_policy == 1) {
+                        v = (blockIdx.x + 1u + a) % p.nblocks;
+                    } else {
+                        rng = rng * 1664525u + 1013904223u;
+                        v = (u32)(((unsigned long long)(rng >> 8) * (p.nblocks - 1u)) >> 24);
+                        v += (v >= blockIdx.x);
+                    }
+                    Ring vr{&p.dqc[v].head, &p.dqc[v].tail, p.dq + (size_t)v * (p.dq_mask + 1u), p.dq_mask};
+                    st_try++;
+                    k = ring_pop(vr, true, lane, e, w.err);
+                    if (k)
+                        st_hit++;
+                }
+                if (k == 0) {
+                    k = ring_pop(w.inj, true, lane, e, w.err);
+                    if (k)
+                        st_inj++;
+                }
+            }
+            if (k == 0) {
+                // stop when every graph is done, on abort, timeout or cancel
+                st_idle++;
+                int stop = 0;
+                if (lane == 0) {
+                    if (vld32(&p.ctl->graphs_left) == 0u || vldi(&p.ctl->abort_code) != 0) {
+                        stop = 1;
+                    } else if (globaltimer() > deadline) {
+                        atomicCAS(&p.ctl->abort_code, 0, TG_ERR_TIMEOUT);
+                        stop = 1;
+                    } else if (p.cancel && (idle & 15u) == 0u && *p.cancel != 0u) {
+                        atomicCAS(&p.ctl->abort_code, 0, TG_ERR_CANCELLED);
+                        stop = 1;
+                    }
+                    if (w.err) {
+                        atomicCAS(&p.ctl->abort_code, 0, TG_ERR_INTERNAL);
+                        stop = 1;
+                    }
+                    if (stop)
+                        *(volatile int *)&s_stop = 1;
+                    vst32(&p.thief_slots[my_slot * 32u], 0u);
+                    __threadfence_block();
+                    *(volatile int *)&s_thief = 0;
+                }
+                if (__shfl_sync(kFull, stop, 0))
+                    break;
+                idle++;
+                __nanosleep(backoff);
+                backoff = min(backoff * 2u, 4096u);
+                continue;
+            }
+            if (lane == 0) {
+                vst32(&p.thief_slots[my_slot * 32u], 0u);
+                *(volatile int *)&s_thief = 0;
+            }
+            backoff = 256;
+        }
+        st_iters++;
+
+        // ---- read the activations' tasks
+        bool act = lane < k && (u32)e != kEmpty32;
+        if (act && ((u32)e & 0x7FFFFFFFu) >= p.node_cap) {
+            w.err = 3;   // never produced by the scheduler: treat as a fault, touch nothing
+            act = false;
+        }
+        u32 u = 0, insum = 0;
+        bool strong = false;
+        if (act) {
+            u = (u32)e & 0x7FFFFFFFu;
+            strong = ((u32)e & kStrongBit) != 0u;
+            insum = (u32)(e >> 32);
+        }
+        uint4 imm = make_uint4(0, 0, 0, 0);
+        uint2 stt = make_uint2(0, 0);
+        u32 gid = 0;
+        if (act) {
+            imm = __ldg(reinterpret_cast<const uint4 *>(&p.slots[u]));
+            stt = __ldcg(reinterpret_cast<const uint2 *>(&p.slots[u].cnt));
+            gid = __ldg(&p.gidv[u]);
+        }
+        i32 gstatus = 0;
+        u32 seed = 0, cap = 0;
+        if (act) {
+            gstatus = vldi(&p.descs[gid].status);
+            seed = __ldg(&p.descs[gid].seed);
+            cap = __ldg(&p.descs[gid].exec_cap);
+        }
+        const u32 succ_off = imm.x;
+        const u32 succ_cnt = imm.y & 0xFFFFu;
+        const u32 indeg = imm.y >> 16;
+        const u32 rounds = imm.z & 0xFFFFu;
+        const u32 kind = (imm.z >> 16) & 0xFFu;
+        const u32 arg = imm.z >> 24;
+        const u32 lid = imm.w;
+        const bool run = act && gstatus == 0;
+        const u32 U = run ? (kind == TG_STATIC ? succ_cnt : 1u) : 0u;
+
+        // reserve the pending count of every activation this warp may push
+        // before any of them becomes visible (ordered by the fence below)
+        {
+            u32 rem = __ballot_sync(kFull, run);
+            while (rem) {
+                int l = __ffs(rem) - 1;
+                u32 g = __shfl_sync(kFull, gid, l);
+                bool in = run && gid == g;
+                u32 m = __ballot_sync(kFull, in);
+                u32 sumU = __reduce_add_sync(kFull, in ? U : 0u);
+                if (lane == l && sumU)
+                    atomicAdd(&p.descs[g].pe, (u64)sumU);
+                rem &= ~m;
+            }
+        }
+        // a strong activation consumed its join word: re-arm it for the next
+        // round (composes with releases of that round that arrive early)
+        if (act && strong)
+            atomicAdd(&p.slots[u].W, (u64)indeg - ((u64)insum << 32));
+
+        // ---- payload
+        u32 x = 0;
+        const u32 iter = stt.x & ~kInflight;
+        if (run) {
+            x = task_payload(lid, iter, insum, rounds);
+            p.outv[u] = x;
+            __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt),
+                   make_uint2((iter + 1u) | (race_check ? kInflight : 0u), mix32(stt.y ^ x)));
+            st_tasks++;
+        }
+        my_push[lane] = 0;
+        my_keep[lane] = 0;
+        __syncwarp();
+        fence_acq_rel_gpu();   // outputs, state and reservations before any release
+
+        // New activations are staged in shared memory.  Each target's
+        // in-flight flag is set (and checked) first; this task's own flag is
+        // released only after all of its checks returned, and only then are
+        // the activations published.  A task that pushes itself hands its
+        // flag to the new activation.
+        u32 ns = 0;   // staged entries (warp-uniform)
+        u32 racy = kEmpty32;   // graph whose activation found a target in flight
+
+        // ---- condition tasks: jump to successors[r]
+        {
+            bool has = false;
+            u64 ent = 0;
+            u32 t = 0;
+            if (run && kind != TG_STATIC) {
+                int r = cond_index(kind, arg, seed, lid, iter, succ_cnt);
+                if (r >= 0 && (u32)r < succ_cnt) {
+                    t = __ldg(&p.edges[succ_off + (u32)r]);
+                    ent = ((u64)x << 32) | (u64)t;
+                    has = true;
+                    my_push[lane] += 1u;
+                }
+            }
+            u32 fl = 0;
+            if (has && race_check) {
+                if (t == u)
+                    my_keep[lane] = 1u;
+                else
+                    fl = atomicOr(&p.slots[t].cnt, kInflight);
+            }
+            stage(w, my_stage, ns, has, ent, lane, st_spill);
+            if (fl & kInflight)
+                racy = gid;
+        }
+
+        // ---- static tasks: release every successor (flattened over the warp)
+        {
+            const u32 c = (run && kind == TG_STATIC) ? succ_cnt : 0u;
+            u32 incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                u32 y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            const u32 total = __shfl_sync(kFull, incl, 31);
+            const u32 excl = incl - c;
+            for (u32 base = 0; base < total; base += 64u) {
+                u32 s_[2], xo_[2], ow_[2], uo_[2], go_[2];
+                u64 old_[2];
+                bool v_[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const u32 ei = base + (u32)j * 32u + (u32)lane;
+                    v_[j] = ei < total;
+                    const u32 eq = v_[j] ? ei : total - 1u;
+                    int o = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        u32 ex = __shfl_sync(kFull, excl, o + step);
+                        if (ex <= eq)
+                            o += step;
+                    }
+                    const u32 off_o = __shfl_sync(kFull, succ_off, o);
+                    const u32 ex_o = __shfl_sync(kFull, excl, o);
+                    xo_[j] = __shfl_sync(kFull, x, o);
+                    uo_[j] = __shfl_sync(kFull, u, o);
+                    go_[j] = __shfl_sync(kFull, gid, o);
+                    ow_[j] = (u32)o;
+                    s_[j] = v_[j] ? __ldg(&p.edges[off_o + (eq - ex_o)]) : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    old_[j] = v_[j] ? atomicAdd(&p.slots[s_[j]].W, ((u64)xo_[j] << 32) - 1ull) : 0ull;
+                u32 fl_[2] = {0u, 0u};
+                bool has_[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    has_[j] = v_[j] && (u32)old_[j] == 1u;
+                    if (has_[j]) {
+                        atomicAdd(&my_push[ow_[j]], 1u);
+                        if (race_check) {
+                            if (s_[j] == uo_[j])
+                                my_keep[ow_[j]] = 1u;
+                            else
+                                fl_[j] = atomicOr(&p.slots[s_[j]].cnt, kInflight);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const u64 ent = ((u64)((u32)(old_[j] >> 32) + xo_[j]) << 32) | kStrongBit | (u64)s_[j];
+                    stage(w, my_stage, ns, has_[j], ent, lane, st_spill);
+                    if (fl_[j] & kInflight)
+                        racy = go_[j];
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- a race poisons the graph in which it was found
+        if (racy != kEmpty32)
+            atomicCAS(&p.descs[racy].status, 0, TG_ERR_RACE);
+
+        // ---- release own in-flight flags, then publish the staged activations
+        if (race_check) {
+            if (run && my_keep[lane] == 0u)
+                p.slots[u].cnt = iter + 1u;
+            fence_acq_rel_gpu();
+        }
+        publish(w, my_stage, ns, lane, st_spill);
+        __syncwarp();
+
+        // ---- settle the pending counts: + pushed - reserved - executed
+        {
+            const u32 P = act ? my_push[lane] : 0u;
+            u32 rem = __ballot_sync(kFull, act);
+            while (rem) {
+                int l = __ffs(rem) - 1;
+                u32 g = __shfl_sync(kFull, gid, l);
+                bool in = act && gid == g;
+                u32 m = __ballot_sync(kFull, in);
+                u32 sumP = __reduce_add_sync(kFull, in ? P : 0u);
+                u32 sumU = __reduce_add_sync(kFull, in ? U : 0u);
+                if (lane == l) {
+                    const u32 E = (u32)__popc(m);
+                    const long long d = (long long)sumP - (long long)sumU - (long long)E;
+                    const u64 delta = ((u64)E << 32) + (u64)d;
+                    const u64 old = atomicAdd(&p.descs[g].pe, delta);
+                    const u64 nw = old + delta;
+                    if ((u32)(nw >> 32) > cap)
+                        atomicCAS(&p.descs[g].status, 0, TG_ERR_EXEC_LIMIT);
+                    if ((u32)nw == 0u)
+                        atomicSub(&p.ctl->graphs_left, 1u);
+                }
+                rem &= ~m;
+            }
+        }
+        if (w.err) {
+            if (lane == 0)
+                atomicCAS(&p.ctl->abort_code, 0, TG_ERR_INTERNAL);
+            break;
+        }
+        // a busy warp also honours the time limit and aborts
+        if ((st_iters & 63u) == 0u) {
+            int stop = 0;
+            if (lane == 0) {
+                if (vldi(&p.ctl->abort_code) != 0)
+                    stop = 1;
+                else if (globaltimer() > deadline) {
+                    atomicCAS(&p.ctl->abort_code, 0, TG_ERR_TIMEOUT);
+                    stop = 1;
+                }
+            }
+            if (__shfl_sync(kFull, stop, 0))
+                break;
+        }
+    }
+
+    if (lane == 0) {
+        atomicAdd(&s_stats[ST_POP_LOCAL], st_local);
+        atomicAdd(&s_stats[ST_POP_OWN], st_own);
+        atomicAdd(&s_stats[ST_STEAL_TRY], st_try);
+        atomicAdd(&s_stats[ST_STEAL_HIT], st_hit);
+        atomicAdd(&s_stats[ST_INJECT], st_inj);
+        atomicAdd(&s_stats[ST_SPILL], st_spill);
+        atomicAdd(&s_stats[ST_IDLE], st_idle);
+        atomicAdd(&s_stats[ST_ITERS], st_iters);
+    }
+    // tasks are counted per lane
+    atomicAdd(&s_stats[ST_TASKS], st_tasks);
+    __syncthreads();
+    if (threadIdx.x < ST_COUNT)
+        p.stats[(size_t)blockIdx.x * ST_COUNT + threadIdx.x] = s_stats[threadIdx.x];
+}
+
+// ---------------------------------------------------------------------------
+// re-arm: state of every graph of the launch, queues, sources (Algorithm 8)
+// grid = (ceil(max_n / 1024), n_graphs)
+// ---------------------------------------------------------------------------
+__global__ void rearm_kernel(KParams p)
+{
+    const u32 gi = blockIdx.y;
+    const u32 gid = p.lt ? p.lt[gi].gid : p.single_gid;
+    const u32 inj_base = p.lt ? p.lt[gi].inj_base : 0u;
+    GDesc &D = p.descs[gid];
+    const u32 n = D.n;
+    const u32 off = D.node_off;
+    const u32 first = blockIdx.x * 1024u;
+    for (u32 i = first + threadIdx.x; i < n && i < first + 1024u; i += blockDim.x) {
+        const u32 u = off + i;
+        const u32 deg = p.slots[u].deg;
+        p.slots[u].W = (u64)(deg >> 16);
+        *reinterpret_cast<uint2 *>(&p.slots[u].cnt) = make_uint2(0u, 0u);
+        p.outv[u] = 0u;
+    }
+    if (blockIdx.x == 0) {
+        for (u32 s = threadIdx.x; s < D.n_src; s += blockDim.x)
+            p.inj[(inj_base + s) & p.inj_mask] = (u64)p.edges[D.src_off + s];
+        if (threadIdx.x == 0) {
+            D.pe = (u64)D.n_src;
+            D.status = 0;
+        }
+    }
+    if (gi == 0 && blockIdx.x == 0) {
+        for (u32 b = threadIdx.x; b < p.nblocks; b += blockDim.x) {
+            p.dqc[b].head = 0u;
+            p.dqc[b].tail = 0u;
+        }
+        for (u32 i = threadIdx.x; i < p.nblocks * (u32)ST_COUNT; i += blockDim.x)
+            p.stats[i] = 0ull;
+        for (u32 i = threadIdx.x; i < p.max_thieves; i += blockDim.x)
+            p.thief_slots[i * 32u] = 0u;
+        if (threadIdx.x == 0) {
+            p.ctl->graphs_left = p.n_graphs;
+            p.ctl->abort_code = 0;
+            p.ctl->hungry = 0u;
+            p.ctl->inj.head = 0u;
+            p.ctl->inj.tail = p.total_sources;
+            if (p.cancel)
+                *p.cancel = 0u;
+        }
+    }
+}
+
+// After the scheduler: unfinished graphs take the launch's abort code; every
+// status is mirrored to host-mapped memory.
+__global__ void finalize_kernel(KParams p)
+{
+    for (u32 gi = blockIdx.x * blockDim.x + threadIdx.x; gi < p.n_graphs; gi += gridDim.x * blockDim.x) {
+        const u32 gid = p.lt ? p.lt[gi].gid : p.single_gid;
+        GDesc &D = p.descs[gid];
+        i32 st = D.status;
+        if (st == 0 && (u32)D.pe != 0u) {
+            i32 ab = p.ctl->abort_code;
+            st = ab != 0 ? ab : TG_ERR_INTERNAL;
+            D.status = st;
+        }
+        if (p.status_out)
+            p.status_out[gid] = st;
+    }
+}
+
+__global__ void clear_kernel(u64 *slots, size_t count)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        slots[i] = kEmpty;
+}
+
+// ---------------------------------------------------------------------------
+// roofline kernels
+// ---------------------------------------------------------------------------
+// The payload alone on ids 0..count-1 (iter 0, insum 0): the integer-ALU
+// ceiling of the scheduler's execute step.  Four independent chains per
+// thread give the issue slots enough independent work.
+__global__ void bench_payload_kernel(u64 count, u32 rounds, u32 *checksum)
+{
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    u32 acc = 0;
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < count; i += 4 * stride) {
+        u32 a = task_payload((u32)i, 0u, 0u, rounds);
+        u32 b = i + stride < count ? task_payload((u32)(i + stride), 0u, 0u, rounds) : 0u;
+        u32 c = i + 2 * stride < count ? task_payload((u32)(i + 2 * stride), 0u, 0u, rounds) : 0u;
+        u32 d = i + 3 * stride < count ? task_payload((u32)(i + 3 * stride), 0u, 0u, rounds) : 0u;
+        acc ^= a ^ b ^ c ^ d;
+    }
+    for (int o = 16; o; o >>= 1)
+        acc ^= __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0)
+        atomicXor(checksum, acc);
+}
+
+// `count` returning 64-bit atomicAdd at pseudo-random words of a footprint.
+__global__ void bench_atomics_kernel(u64 *words, u64 footprint, u64 count, u64 *sink)
+{
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    u64 acc = 0;
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < count; i += stride) {
+        u32 h = mix32((u32)i ^ mix32((u32)(i >> 32) + 0x51ED27u));
+        u64 a = ((u64)h * footprint) >> 32;
+        acc += atomicAdd(&words[a], 0x100000001ull);
+    }
+    if (acc == 0x123456789ull)
+        *sink = acc;
+}
+
+}  // namespace
+
+size_t sched_dyn_smem(u32 smem_entries, u32 warps)
+{
+    return ((size_t)smem_entries + (size_t)warps * kStage) * sizeof(u64);
+}
+
+cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(sched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel, threads, dyn_smem);
+}
+
+cudaError_t launch_rearm(const KParams &p, cudaStream_t st)
+{
+    dim3 grid((p.max_n + 1023u) / 1024u, p.n_graphs);
+    if (grid.x == 0)
+        grid.x = 1;
+    rearm_kernel<<<grid, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t st)
+{
+    sched_kernel<<<blocks, threads, sched_dyn_smem(p.smem_mask + 1u, (u32)threads / 32u), st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const KParams &p, cudaStream_t st)
+{
+    u32 blocks = (p.n_graphs + 255u) / 256u;
+    finalize_kernel<<<blocks ? blocks : 1u, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear(u64 *slots, size_t count, cudaStream_t st)
+{
+    if (count == 0)
+        return cudaSuccess;
+    size_t blocks = (count + 255) / 256;
+    if (blocks > 65535)
+        blocks = 65535;
+    clear_kernel<<<(unsigned)blocks, 256, 0, st>>>(slots, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bench_payload(u64 count, u32 rounds, u32 *checksum, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    bench_payload_kernel<<<sms * 8, 256, 0, st>>>(count, rounds, checksum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    bench_atomics_kernel<<<sms * 8, 256, 0, st>>>(words, footprint, count, sink);
+    return cudaGetLastError();
+}
+
+}  // namespace tg

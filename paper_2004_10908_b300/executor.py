@@ -1,0 +1,127 @@
+"""Executor: a context on one CUDA device whose arena and stream come from
+PyTorch, with graph handles that own their device pools.  A thin layer over
+the C-ABI names in binding.py."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding as B
+
+
+class GraphHandle:
+    def __init__(self, ex: "Executor", handle: int, n: int, m: int, name: str = ""):
+        self.ex, self.handle, self.n, self.m, self.name = ex, handle, n, m, name
+
+    def info(self) -> dict:
+        return B.tg_graph_get_info(self.handle)
+
+    def destroy(self):
+        if self.handle:
+            B.tg_graph_destroy(self.ex.ctx, self.handle)
+            self.handle = None
+
+
+class Batch:
+    def __init__(self, ex: "Executor", handle: int, graphs):
+        self.ex, self.handle, self.graphs = ex, handle, list(graphs)
+
+    def launch(self):
+        st = B.tg_batch_launch(self.ex.ctx, self.handle)
+        if st != B.TG_OK:
+            raise B.TgError(st, "tg_batch_launch")
+
+    def wait(self):
+        return B.tg_batch_wait(self.ex.ctx, self.handle, len(self.graphs))
+
+    def destroy(self):
+        if self.handle:
+            B.tg_batch_destroy(self.ex.ctx, self.handle)
+            self.handle = None
+
+
+class Executor:
+    """Device-resident task-graph executor on the current CUDA device.
+
+    arena_bytes: size of the torch-allocated device arena the library
+    sub-allocates; stream: a torch.cuda.Stream (default: a new one);
+    opts: any tg_ctx_opts field (worker_blocks, warps_per_block, deque_depth,
+    steal_policy, max_steal, smem_ring, flags, time_limit_ns, exec_cap,
+    mem_budget_bytes, max_nodes, max_edges)."""
+
+    def __init__(self, arena_bytes: int = 1 << 30, stream=None, **opts):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        B.load()
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+        o = B.tg_ctx_opts()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.ctx = B.tg_ctx_create(self.arena.data_ptr(), int(arena_bytes), self.stream.cuda_stream, o)
+
+    # -- graphs -----------------------------------------------------------
+    def create(self, kinds, params, src, dst, seed=0, weak=None, name=""):
+        st, h = B.tg_graph_create(self.ctx, kinds, params, src, dst, seed, weak)
+        if st != B.TG_OK:
+            raise B.TgError(st, f"tg_graph_create {name}")
+        return GraphHandle(self, h, len(kinds), len(src), name)
+
+    def graph(self, g, weak=None):
+        """Upload a workloads.Graph-like object (kinds, params, src, dst, seed)."""
+        return self.create(g.kinds, g.params, g.src, g.dst, g.seed, weak, getattr(g, "name", ""))
+
+    def run(self, gh: GraphHandle) -> int:
+        return B.tg_run(self.ctx, gh.handle)
+
+    def submit(self, gh: GraphHandle) -> int:
+        st, t = B.tg_submit(self.ctx, gh.handle)
+        if st != B.TG_OK:
+            raise B.TgError(st, "tg_submit")
+        return t
+
+    def poll(self, ticket) -> int:
+        return B.tg_poll(self.ctx, ticket)
+
+    def wait(self, ticket) -> int:
+        return B.tg_wait(self.ctx, ticket)
+
+    def cancel(self):
+        return B.tg_cancel(self.ctx)
+
+    def result(self, gh: GraphHandle):
+        return B.tg_result_copy(self.ctx, gh.handle, gh.n)
+
+    def batch(self, graphs) -> Batch:
+        st, h = B.tg_batch_create(self.ctx, [g.handle for g in graphs])
+        if st != B.TG_OK:
+            raise B.TgError(st, "tg_batch_create")
+        return Batch(self, h, graphs)
+
+    def run_batch(self, graphs):
+        return B.tg_run_batch(self.ctx, [g.handle for g in graphs])
+
+    # -- measurement --------------------------------------------------------
+    def stats(self) -> dict:
+        return B.tg_ctx_get_stats(self.ctx)
+
+    def opts(self) -> dict:
+        return B.tg_ctx_get_opts(self.ctx)
+
+    def bench_payload(self, count, rounds):
+        return B.tg_bench_payload(self.ctx, count, rounds)
+
+    def bench_atomics(self, count, footprint_words):
+        return B.tg_bench_atomics(self.ctx, count, footprint_words)
+
+    def close(self):
+        if self.ctx:
+            B.tg_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
