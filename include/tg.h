@@ -201,6 +201,27 @@ int tg_ctx_get_opts(const tg_ctx *ctx, tg_ctx_opts *opts);
 int tg_bench_payload(tg_ctx *ctx, uint64_t count, uint32_t rounds, uint64_t *ns, uint32_t *checksum);
 int tg_bench_atomics(tg_ctx *ctx, uint64_t count, uint64_t footprint_words, uint64_t *ns);
 
+/* Run one graph without allocating anything (the paper has no counterpart:
+ * this exists for callers that cannot allocate device memory, e.g. code
+ * inside another framework's memory pool or a plugin handed fixed buffers).
+ * All scratch memory lives in one fixed-size array inside the library that
+ * every GPU loading the library holds until the process exits; no cudaMalloc,
+ * cudaFree or other allocating routine is called.
+ *   kinds[n], params[n]       device arrays, as for tg_graph_create
+ *   succ_off[n+1], succ[m]    device arrays: task v's successors, in insertion
+ *                             order, are succ[succ_off[v] .. succ_off[v+1])
+ *   out[n], cnt[n], dig[n]    device outputs (any may be NULL)
+ *   cuda_stream               stream the work is enqueued on; the call
+ *                             synchronises it before returning
+ * Limits: n <= 65536 tasks and m <= 262144 edges, else TG_ERR_BUDGET.
+ * Returns the validation status (as tg_graph_create) or the run's status.
+ * Every call shares the one scratch array: calls that overlap on the GPU
+ * race.  The first call on a device sets that device up (looks up the
+ * array's address), so make it before any stream capture. */
+int tg_run_noalloc(uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
+                   const uint32_t *succ_off, const uint32_t *succ, uint32_t n_edges, uint32_t seed,
+                   uint32_t *out, uint32_t *cnt, uint32_t *dig, void *cuda_stream);
+
 const char *tg_strerror(int status);
 
 #ifdef __cplusplus

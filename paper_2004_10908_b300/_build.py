@@ -7,7 +7,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libtg.so")
-SOURCES = [os.path.join(CSRC, "tg_host.cpp"), os.path.join(CSRC, "tg_kernels.cu")]
+SOURCES = [os.path.join(CSRC, "tg_host.cpp"), os.path.join(CSRC, "tg_kernels.cu"),
+           os.path.join(CSRC, "tg_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "tg_internal.h"), os.path.join(ROOT, "include", "tg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -89,6 +89,7 @@ SIGNATURES = {
     "tg_ctx_get_opts": (ctypes.c_int, [_vp, ctypes.POINTER(tg_ctx_opts)]),
     "tg_bench_payload": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "tg_bench_atomics": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(_u64)]),
+    "tg_run_noalloc": (ctypes.c_int, [_u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]),
     "tg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -245,3 +246,11 @@ def tg_bench_atomics(ctx, count, footprint_words):
     ns = _u64(0)
     _check(load().tg_bench_atomics(_vp(ctx), count, footprint_words, ctypes.byref(ns)), "tg_bench_atomics")
     return ns.value
+
+
+def tg_run_noalloc(n_nodes, kinds_ptr, params_ptr, succ_off_ptr, succ_ptr, n_edges, seed,
+                   out_ptr, cnt_ptr, dig_ptr, cuda_stream) -> int:
+    """Device pointers in, device pointers out; see include/tg.h."""
+    return load().tg_run_noalloc(n_nodes, _vp(kinds_ptr), _vp(params_ptr), _vp(succ_off_ptr), _vp(succ_ptr),
+                                 n_edges, seed & 0xFFFFFFFF, _vp(out_ptr), _vp(cnt_ptr), _vp(dig_ptr),
+                                 _vp(cuda_stream))
