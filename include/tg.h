@@ -185,6 +185,7 @@ typedef struct {
     uint64_t spills;           /* batches moved from shared memory to a public deque */
     uint64_t idle_loops;       /* warp iterations that found no work */
     uint64_t warp_iters;       /* warp iterations that executed work */
+    uint64_t pops_hand;        /* batches a warp kept from its own previous step */
     uint64_t kernel_ns;        /* device time of the last scheduler launch */
     uint32_t worker_blocks, warps_per_block;
 } tg_stats;

@@ -54,7 +54,7 @@ class tg_graph_info(ctypes.Structure):
 class tg_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("tasks", "pops_local", "pops_own", "steal_attempts", "steal_hits", "inject_pops",
-                 "spills", "idle_loops", "warp_iters", "kernel_ns")] + \
+                 "spills", "idle_loops", "warp_iters", "pops_hand", "kernel_ns")] + \
                [("worker_blocks", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32)]
 
     def as_dict(self):

@@ -322,7 +322,7 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
         delete c;
         return TG_ERR_CUDA;
     }
-    int max_blocks = per_sm * c->sm_count;
+    int max_blocks = std::min(per_sm * c->sm_count, 1024);   // work-available bitmap size
     c->nblocks = o.worker_blocks > 0 ? std::min(o.worker_blocks, max_blocks) : max_blocks;
     o.worker_blocks = c->nblocks;
 
@@ -913,6 +913,7 @@ int tg_ctx_get_stats(tg_ctx *c, tg_stats *st)
         st->spills += s[ST_SPILL];
         st->idle_loops += s[ST_IDLE];
         st->warp_iters += s[ST_ITERS];
+        st->pops_hand += s[ST_HAND];
     }
     if (c->timed) {
         float ms = 0.f;

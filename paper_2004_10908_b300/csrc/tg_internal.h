@@ -63,11 +63,13 @@ struct alignas(128) LaunchCtl {
     u32 hungry;
     u32 pad2[31];
     QCtr inj;
+    u32 avail[32];   // bit b: block b's public deque may hold work (blocks < 1024)
+    u32 pad3[96];
 };
 
 enum StatIdx {
     ST_TASKS = 0, ST_POP_LOCAL, ST_POP_OWN, ST_STEAL_TRY, ST_STEAL_HIT, ST_INJECT,
-    ST_SPILL, ST_IDLE, ST_ITERS, ST_COUNT = 16
+    ST_SPILL, ST_IDLE, ST_ITERS, ST_HAND, ST_COUNT = 16
 };
 
 constexpr u32 kEmpty32 = 0xFFFFFFFFu;

@@ -23,6 +23,9 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kSpinLimit = 1 << 20;     // bounded waits on a slot (iterations)
 constexpr int kCasTries = 256;
 constexpr u32 kStage = 256;             // staged activations per warp (shared memory)
+constexpr int kRelUnroll = 4;           // successor releases in flight per lane
+constexpr u32 kPerLaneMax = 16;         // widest fan-out released lane by lane
+constexpr u32 kHandMax = 2;             // narrowest step output kept by the warp itself
 
 // ---------------------------------------------------------------------------
 // arithmetic of the method (payload, condition hash, digest)
@@ -213,6 +216,8 @@ struct WarpCtx {
     Ring own;        // block's public deque
     Ring inj;        // shared injection queue
     u32 high_water;  // local ring size above which new work goes public
+    u32 *avail_word; // this block's word / bit in the work-available bitmap
+    u32 avail_bit;
     int err;
 };
 
@@ -232,10 +237,28 @@ __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u6
     if (__ballot_sync(kFull, pub) != 0) {
         if (lane == 0)
             spill_ctr++;
-        if (!ring_push(w.own, pub, ent, lane, w.err))
-            if (!ring_push(w.inj, pub, ent, lane, w.err))
-                w.err = 2;
+        if (ring_push(w.own, pub, ent, lane, w.err)) {
+            if (lane == 0 && (vld32(w.avail_word) & w.avail_bit) == 0u)
+                atomicOr(w.avail_word, w.avail_bit);
+        } else if (!ring_push(w.inj, pub, ent, lane, w.err)) {
+            w.err = 2;
+        }
     }
+}
+
+// Examine the result of the previous iteration's pending-count update: a
+// graph whose pending count reached zero is complete; one whose execution
+// count passed its cap is poisoned with TG_ERR_EXEC_LIMIT.
+__device__ __forceinline__ void settle_finish(const KParams &p, bool &pend, u64 old, u64 delta, u32 g, u32 cap)
+{
+    if (!pend)
+        return;
+    const u64 nw = old + delta;
+    if ((u32)(nw >> 32) > cap)
+        atomicCAS(&p.descs[g].status, 0, TG_ERR_EXEC_LIMIT);
+    if ((u32)nw == 0u)
+        atomicSub(&p.ctl->graphs_left, 1u);
+    pend = false;
 }
 
 // Stage the new activations of the lanes with `has` in the warp's buffer;
@@ -294,6 +317,8 @@ __global__ void sched_kernel(KParams p)
     __syncthreads();
 
     const bool race_check = (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
+    const bool single = p.lt == nullptr;   // one graph: every activation has gid == single_gid
+    const u32 single_cap = single ? __ldg(&p.descs[p.single_gid].exec_cap) : 0u;
     const u64 t0 = globaltimer();
     const u64 deadline = t0 + p.time_limit_ns;
 
@@ -306,110 +331,160 @@ __global__ void sched_kernel(KParams p)
     // new activations go to the public deque where other blocks steal them
     w.high_water = min(ring_n / 2u, max(64u, (blockDim.x / 32u) * 32u));
     w.err = 0;
+    w.avail_word = &p.ctl->avail[blockIdx.x >> 5];
+    w.avail_bit = 1u << (blockIdx.x & 31u);
     u32 *my_push = s_push + warp * 32;
     u32 *my_keep = s_keep + warp * 32;
     u64 *my_stage = s_ring + ring_n + (size_t)warp * kStage;
 
     u64 st_tasks = 0, st_local = 0, st_own = 0, st_try = 0, st_hit = 0, st_inj = 0, st_spill = 0,
-        st_idle = 0, st_iters = 0;
+        st_idle = 0, st_iters = 0, st_hand = 0;
     u32 rng = mix32(blockIdx.x * 0x9E3779B9U + (u32)warp * 0x85EBCA6BU + 1u);
+    bool pend = false;      // a pending-count update whose result is not examined yet
+    u64 pend_old = 0, pend_delta = 0;
+    u32 pend_g = 0, pend_cap = 0;
     u32 backoff = 256;
     const u32 my_slot = blockIdx.x % p.max_thieves;
     u32 idle = 0;
+    // activations this warp kept for itself (lanes [0, nh) of `hand`)
+    u64 hand = kEmpty;
+    int nh = 0;
+    // per-lane cache of the lane's graph descriptor; the status word is
+    // re-read every 16 activations, so a poisoned graph drains soon after
+    u32 c_gid = kEmpty32, c_seed = 0, c_cap = 0, c_age = 0;
+    i32 c_status = 0;
 
     for (;;) {
-        // ---- take work from the block's shared-memory ring
-        u64 e;
-        int k = ring_pop(w.local, false, lane, e, w.err);
-        if (k) {
-            st_local++;
+        u64 e = kEmpty;
+        int k = 0;
+        if (nh) {
+            e = hand;
+            k = nh;
+            nh = 0;
+            st_hand++;
         } else {
-            // ---- idle.  One warp per block at a time is the block's thief
-            // (Alg. 6/7): it probes the own public deque, up to max_steal
-            // victims and the injection queue, and is the only warp of the
-            // block that polls launch-wide state.  The other idle warps wait
-            // on shared memory, so idle polling never floods L2.
-            if (*(volatile int *)&s_stop)
-                break;
-            int am = 0;
-            if (lane == 0) {
-                am = atomicCAS(&s_thief, 0, 1) == 0;
-                // at most max_thieves blocks steal / poll at once (the paper's
-                // bound on wasteful steals); slots live on separate lines
-                if (am && atomicCAS(&p.thief_slots[my_slot * 32u], 0u, 1u) != 0u) {
-                    *(volatile int *)&s_thief = 0;
-                    am = 2;
-                }
-            }
-            am = __shfl_sync(kFull, am, 0);
-            if (am != 1) {
-                st_idle++;
-                __nanosleep(am == 2 ? backoff : p.idle_sleep_ns);
-                if (am == 2)
-                    backoff = min(backoff * 2u, 4096u);
-                continue;
-            }
-            k = ring_pop(w.own, false, lane, e, w.err);
+            k = ring_pop(w.local, false, lane, e, w.err);
             if (k) {
-                st_own++;
+                st_local++;
             } else {
-                for (u32 a = 0; a < p.max_steal && k == 0 && p.nblocks > 1; ++a) {
-                    u32 v;
+                settle_finish(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+                // ---- idle.  One warp per block at a time is the block's thief
+                // (Alg. 6/7), and at most max_thieves blocks steal at once; only
+                // thieves poll launch-wide state, the other idle warps wait on
+                // shared memory, so idle polling never floods L2.
+                if (*(volatile int *)&s_stop)
+                    break;
+                int am = 0;
+                if (lane == 0) {
+                    am = atomicCAS(&s_thief, 0, 1) == 0;
+                    if (am && atomicCAS(&p.thief_slots[my_slot * 32u], 0u, 1u) != 0u) {
+                        *(volatile int *)&s_thief = 0;
+                        am = 2;
+                    }
+                }
+                am = __shfl_sync(kFull, am, 0);
+                if (am != 1) {
+                    st_idle++;
+                    __nanosleep(am == 2 ? backoff : p.idle_sleep_ns);
+                    if (am == 2)
+                        backoff = min(backoff * 2u, 4096u);
+                    continue;
+                }
+                k = ring_pop(w.own, false, lane, e, w.err);
+                if (k) {
+                    st_own++;
+                } else {
+                    if (lane == 0 && (vld32(w.avail_word) & w.avail_bit) != 0u) {
+                        atomicAnd(w.avail_word, ~w.avail_bit);
+                        if (ring_size(w.own) != 0u)
+                            atomicOr(w.avail_word, w.avail_bit);
+                    }
+                    // victims: blocks whose availability bit is set, scanned from
+                    // a random (or, for the ring policy, the next) block
+                    const u32 nwords = (p.nblocks + 31u) >> 5;
+                    u32 word = (u32)lane < nwords ? vld32(&p.ctl->avail[lane]) : 0u;
+                    if ((u32)lane == (blockIdx.x >> 5))
+                        word &= ~(1u << (blockIdx.x & 31u));
+                    const u32 nonempty = __ballot_sync(kFull, word != 0u);
+                    u32 start;
                     if (p.steal_policy == 1) {
-                        v = (blockIdx.x + 1u + a) % p.nblocks;
+                        start = blockIdx.x + 1u;
                     } else {
                         rng = rng * 1664525u + 1013904223u;
-                        v = (u32)(((unsigned long long)(rng >> 8) * (p.nblocks - 1u)) >> 24);
-                        v += (v >= blockIdx.x);
+                        start = (u32)(((unsigned long long)(rng >> 8) * p.nblocks) >> 24);
                     }
-                    Ring vr{&p.dqc[v].head, &p.dqc[v].tail, p.dq + (size_t)v * (p.dq_mask + 1u), p.dq_mask};
-                    st_try++;
-                    k = ring_pop(vr, true, lane, e, w.err);
-                    if (k)
-                        st_hit++;
+                    u32 tries = 0;
+                    if (nonempty) {
+                        for (u32 i = 0; i < nwords && k == 0 && tries < p.max_steal; ++i) {
+                            const u32 wi = ((start >> 5) + i) % nwords;
+                            u32 bits = __shfl_sync(kFull, word, (int)wi);
+                            if (i == 0)
+                                bits &= ~((1u << (start & 31u)) - 1u);
+                            while (bits && k == 0 && tries < p.max_steal) {
+                                const u32 v = wi * 32u + (u32)(__ffs(bits) - 1);
+                                bits &= bits - 1u;
+                                if (v >= p.nblocks)
+                                    break;
+                                Ring vr{&p.dqc[v].head, &p.dqc[v].tail, p.dq + (size_t)v * (p.dq_mask + 1u),
+                                        p.dq_mask};
+                                st_try++;
+                                tries++;
+                                k = ring_pop(vr, true, lane, e, w.err);
+                                if (k) {
+                                    st_hit++;
+                                } else if (lane == 0) {
+                                    // drained: clear the bit, then re-check so a
+                                    // spill that raced with the clear stays visible
+                                    atomicAnd(&p.ctl->avail[v >> 5], ~(1u << (v & 31u)));
+                                    if (ring_size(vr) != 0u)
+                                        atomicOr(&p.ctl->avail[v >> 5], 1u << (v & 31u));
+                                }
+                            }
+                        }
+                    }
+                    if (k == 0) {
+                        k = ring_pop(w.inj, true, lane, e, w.err);
+                        if (k)
+                            st_inj++;
+                    }
                 }
                 if (k == 0) {
-                    k = ring_pop(w.inj, true, lane, e, w.err);
-                    if (k)
-                        st_inj++;
+                    // stop when every graph is done, on abort, timeout or cancel
+                    st_idle++;
+                    int stop = 0;
+                    if (lane == 0) {
+                        if (vld32(&p.ctl->graphs_left) == 0u || vldi(&p.ctl->abort_code) != 0) {
+                            stop = 1;
+                        } else if (globaltimer() > deadline) {
+                            atomicCAS(&p.ctl->abort_code, 0, TG_ERR_TIMEOUT);
+                            stop = 1;
+                        } else if (p.cancel && (idle & 15u) == 0u && *p.cancel != 0u) {
+                            atomicCAS(&p.ctl->abort_code, 0, TG_ERR_CANCELLED);
+                            stop = 1;
+                        }
+                        if (w.err) {
+                            atomicCAS(&p.ctl->abort_code, 0, TG_ERR_INTERNAL);
+                            stop = 1;
+                        }
+                        if (stop)
+                            *(volatile int *)&s_stop = 1;
+                        vst32(&p.thief_slots[my_slot * 32u], 0u);
+                        __threadfence_block();
+                        *(volatile int *)&s_thief = 0;
+                    }
+                    if (__shfl_sync(kFull, stop, 0))
+                        break;
+                    idle++;
+                    __nanosleep(backoff);
+                    backoff = min(backoff * 2u, 4096u);
+                    continue;
                 }
-            }
-            if (k == 0) {
-                // stop when every graph is done, on abort, timeout or cancel
-                st_idle++;
-                int stop = 0;
                 if (lane == 0) {
-                    if (vld32(&p.ctl->graphs_left) == 0u || vldi(&p.ctl->abort_code) != 0) {
-                        stop = 1;
-                    } else if (globaltimer() > deadline) {
-                        atomicCAS(&p.ctl->abort_code, 0, TG_ERR_TIMEOUT);
-                        stop = 1;
-                    } else if (p.cancel && (idle & 15u) == 0u && *p.cancel != 0u) {
-                        atomicCAS(&p.ctl->abort_code, 0, TG_ERR_CANCELLED);
-                        stop = 1;
-                    }
-                    if (w.err) {
-                        atomicCAS(&p.ctl->abort_code, 0, TG_ERR_INTERNAL);
-                        stop = 1;
-                    }
-                    if (stop)
-                        *(volatile int *)&s_stop = 1;
                     vst32(&p.thief_slots[my_slot * 32u], 0u);
-                    __threadfence_block();
                     *(volatile int *)&s_thief = 0;
                 }
-                if (__shfl_sync(kFull, stop, 0))
-                    break;
-                idle++;
-                __nanosleep(backoff);
-                backoff = min(backoff * 2u, 4096u);
-                continue;
+                backoff = 256;
             }
-            if (lane == 0) {
-                vst32(&p.thief_slots[my_slot * 32u], 0u);
-                *(volatile int *)&s_thief = 0;
-            }
-            backoff = 256;
         }
         st_iters++;
 
@@ -432,14 +507,18 @@ __global__ void sched_kernel(KParams p)
         if (act) {
             imm = __ldg(reinterpret_cast<const uint4 *>(&p.slots[u]));
             stt = __ldcg(reinterpret_cast<const uint2 *>(&p.slots[u].cnt));
-            gid = __ldg(&p.gidv[u]);
+            gid = single ? p.single_gid : __ldg(&p.gidv[u]);
         }
-        i32 gstatus = 0;
-        u32 seed = 0, cap = 0;
         if (act) {
-            gstatus = vldi(&p.descs[gid].status);
-            seed = __ldg(&p.descs[gid].seed);
-            cap = __ldg(&p.descs[gid].exec_cap);
+            if (gid != c_gid || c_age >= 16u) {
+                c_seed = __ldg(&p.descs[gid].seed);
+                c_cap = __ldg(&p.descs[gid].exec_cap);
+                c_status = vldi(&p.descs[gid].status);
+                c_gid = gid;
+                c_age = 0;
+            } else {
+                c_age++;
+            }
         }
         const u32 succ_off = imm.x;
         const u32 succ_cnt = imm.y & 0xFFFFu;
@@ -448,12 +527,83 @@ __global__ void sched_kernel(KParams p)
         const u32 kind = (imm.z >> 16) & 0xFFu;
         const u32 arg = imm.z >> 24;
         const u32 lid = imm.w;
-        const bool run = act && gstatus == 0;
-        const u32 U = run ? (kind == TG_STATIC ? succ_cnt : 1u) : 0u;
+        const u32 iter = stt.x & ~kInflight;
 
+        // Successor ids of static tasks are fetched before the payload runs,
+        // so their latency hides under it.  If no lane has more than
+        // kPerLaneMax successors each lane releases its own; otherwise the
+        // edges are flattened over the warp (edge e belongs to the lane
+        // whose exclusive prefix covers it) to spread a wide fan-out.
+        const u32 c = (act && kind == TG_STATIC) ? succ_cnt : 0u;
+        const u32 maxc = __reduce_max_sync(kFull, c);
+        const bool per_lane = maxc <= kPerLaneMax;
+        u32 s_[kRelUnroll], ow_[kRelUnroll];
+        bool v_[kRelUnroll];
+        u32 total = 0, excl = 0;
+        auto fetch_lane = [&](u32 j0) {
+#pragma unroll
+            for (int j = 0; j < kRelUnroll; ++j) {
+                v_[j] = j0 + (u32)j < c;
+                ow_[j] = (u32)lane;
+                s_[j] = v_[j] ? __ldg(&p.edges[succ_off + j0 + (u32)j]) : 0u;
+            }
+        };
+        auto fetch_flat = [&](u32 base) {
+#pragma unroll
+            for (int j = 0; j < kRelUnroll; ++j) {
+                const u32 ei = base + (u32)j * 32u + (u32)lane;
+                v_[j] = ei < total;
+                const u32 eq = v_[j] ? ei : total - 1u;
+                int o = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    u32 ex = __shfl_sync(kFull, excl, o + step);
+                    if (ex <= eq)
+                        o += step;
+                }
+                const u32 off_o = __shfl_sync(kFull, succ_off, o);
+                const u32 ex_o = __shfl_sync(kFull, excl, o);
+                ow_[j] = (u32)o;
+                s_[j] = v_[j] ? __ldg(&p.edges[off_o + (eq - ex_o)]) : 0u;
+            }
+        };
+        if (per_lane) {
+            if (maxc)
+                fetch_lane(0u);
+        } else {
+            u32 incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                u32 y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            total = __shfl_sync(kFull, incl, 31);
+            excl = incl - c;
+            fetch_flat(0u);
+        }
+
+        // the previous iteration's pending-count update arrives meanwhile
+        settle_finish(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+
+        // a strong activation consumed its join word: re-arm it for the next
+        // round (composes with releases of that round that arrive early)
+        if (act && strong)
+            atomicAdd(&p.slots[u].W, (u64)indeg - ((u64)insum << 32));
+
+        // ---- payload
+        const u32 x = act ? task_payload(lid, iter, insum, rounds) : 0u;
+        const u32 dg = mix32(stt.y ^ x);
+
+        const bool run = act && c_status == 0;
+        const u32 U = run ? (kind == TG_STATIC ? succ_cnt : 1u) : 0u;
         // reserve the pending count of every activation this warp may push
-        // before any of them becomes visible (ordered by the fence below)
-        {
+        // before any of them becomes visible (a fence precedes publication)
+        if (single) {
+            const u32 sumU = __reduce_add_sync(kFull, U);
+            if (lane == 0 && sumU)
+                atomicAdd(&p.descs[p.single_gid].pe, (u64)sumU);
+        } else {
             u32 rem = __ballot_sync(kFull, run);
             while (rem) {
                 int l = __ffs(rem) - 1;
@@ -466,103 +616,105 @@ __global__ void sched_kernel(KParams p)
                 rem &= ~m;
             }
         }
-        // a strong activation consumed its join word: re-arm it for the next
-        // round (composes with releases of that round that arrive early)
-        if (act && strong)
-            atomicAdd(&p.slots[u].W, (u64)indeg - ((u64)insum << 32));
-
-        // ---- payload
-        u32 x = 0;
-        const u32 iter = stt.x & ~kInflight;
-        if (run) {
-            x = task_payload(lid, iter, insum, rounds);
-            p.outv[u] = x;
-            __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt),
-                   make_uint2((iter + 1u) | (race_check ? kInflight : 0u), mix32(stt.y ^ x)));
+        if (run)
             st_tasks++;
+        if (!race_check) {
+            // without in-flight flags the state must be visible before any
+            // release makes a later activation of this task possible
+            if (run)
+                __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt), make_uint2(iter + 1u, dg));
+            fence_acq_rel_gpu();
         }
-        my_push[lane] = 0;
-        my_keep[lane] = 0;
+        if (!per_lane) {
+            my_push[lane] = 0;
+            my_keep[lane] = 0;
+        }
         __syncwarp();
-        fence_acq_rel_gpu();   // outputs, state and reservations before any release
 
         // New activations are staged in shared memory.  Each target's
         // in-flight flag is set (and checked) first; this task's own flag is
-        // released only after all of its checks returned, and only then are
-        // the activations published.  A task that pushes itself hands its
-        // flag to the new activation.
-        u32 ns = 0;   // staged entries (warp-uniform)
-        u32 racy = kEmpty32;   // graph whose activation found a target in flight
+        // released -- together with its new count and digest -- only after
+        // all of its checks returned, and only then are the activations
+        // published.  A task that pushes itself hands its flag on.
+        u32 ns = 0;              // staged entries (warp-uniform)
+        u32 racy = kEmpty32;     // graph whose activation found a target in flight
+        u32 mp = 0;              // activations this lane's task pushed (own-lane part)
+        bool keep_self = false;  // this lane's task pushed itself
 
         // ---- condition tasks: jump to successors[r]
-        {
-            bool has = false;
-            u64 ent = 0;
-            u32 t = 0;
-            if (run && kind != TG_STATIC) {
-                int r = cond_index(kind, arg, seed, lid, iter, succ_cnt);
-                if (r >= 0 && (u32)r < succ_cnt) {
-                    t = __ldg(&p.edges[succ_off + (u32)r]);
-                    ent = ((u64)x << 32) | (u64)t;
-                    has = true;
-                    my_push[lane] += 1u;
+        bool c_has = false;
+        u32 c_t = 0, c_fl = 0;
+        if (run && kind != TG_STATIC) {
+            int r = cond_index(kind, arg, c_seed, lid, iter, succ_cnt);
+            if (r >= 0 && (u32)r < succ_cnt) {
+                c_t = __ldg(&p.edges[succ_off + (u32)r]);
+                c_has = true;
+                mp++;
+                if (race_check) {
+                    if (c_t == u)
+                        keep_self = true;
+                    else
+                        c_fl = atomicOr(&p.slots[c_t].cnt, kInflight);
                 }
             }
-            u32 fl = 0;
-            if (has && race_check) {
-                if (t == u)
-                    my_keep[lane] = 1u;
-                else
-                    fl = atomicOr(&p.slots[t].cnt, kInflight);
-            }
-            stage(w, my_stage, ns, has, ent, lane, st_spill);
-            if (fl & kInflight)
-                racy = gid;
         }
 
-        // ---- static tasks: release every successor (flattened over the warp)
-        {
-            const u32 c = (run && kind == TG_STATIC) ? succ_cnt : 0u;
-            u32 incl = c;
+        // ---- static tasks: release every successor
+        if (per_lane) {
+            for (u32 j0 = 0; j0 < maxc; j0 += kRelUnroll) {
+                if (j0)
+                    fetch_lane(j0);
+                u64 old_[kRelUnroll];
+                u32 fl_[kRelUnroll];
+                bool has_[kRelUnroll];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                u32 y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o)
-                    incl += y;
-            }
-            const u32 total = __shfl_sync(kFull, incl, 31);
-            const u32 excl = incl - c;
-            for (u32 base = 0; base < total; base += 64u) {
-                u32 s_[2], xo_[2], ow_[2], uo_[2], go_[2];
-                u64 old_[2];
-                bool v_[2];
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const u32 ei = base + (u32)j * 32u + (u32)lane;
-                    v_[j] = ei < total;
-                    const u32 eq = v_[j] ? ei : total - 1u;
-                    int o = 0;
-#pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        u32 ex = __shfl_sync(kFull, excl, o + step);
-                        if (ex <= eq)
-                            o += step;
-                    }
-                    const u32 off_o = __shfl_sync(kFull, succ_off, o);
-                    const u32 ex_o = __shfl_sync(kFull, excl, o);
-                    xo_[j] = __shfl_sync(kFull, x, o);
-                    uo_[j] = __shfl_sync(kFull, u, o);
-                    go_[j] = __shfl_sync(kFull, gid, o);
-                    ow_[j] = (u32)o;
-                    s_[j] = v_[j] ? __ldg(&p.edges[off_o + (eq - ex_o)]) : 0u;
+                for (int j = 0; j < kRelUnroll; ++j) {
+                    v_[j] = v_[j] && run;
+                    old_[j] = v_[j] ? atomicAdd(&p.slots[s_[j]].W, ((u64)x << 32) - 1ull) : 0ull;
                 }
 #pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    old_[j] = v_[j] ? atomicAdd(&p.slots[s_[j]].W, ((u64)xo_[j] << 32) - 1ull) : 0ull;
-                u32 fl_[2] = {0u, 0u};
-                bool has_[2];
+                for (int j = 0; j < kRelUnroll; ++j) {
+                    fl_[j] = 0u;
+                    has_[j] = v_[j] && (u32)old_[j] == 1u;
+                    if (has_[j]) {
+                        mp++;
+                        if (race_check) {
+                            if (s_[j] == u)
+                                keep_self = true;
+                            else
+                                fl_[j] = atomicOr(&p.slots[s_[j]].cnt, kInflight);
+                        }
+                    }
+                }
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                for (int j = 0; j < kRelUnroll; ++j) {
+                    const u64 ent = ((u64)((u32)(old_[j] >> 32) + x) << 32) | kStrongBit | (u64)s_[j];
+                    stage(w, my_stage, ns, has_[j], ent, lane, st_spill);
+                    if (fl_[j] & kInflight)
+                        racy = gid;
+                }
+            }
+        } else {
+            for (u32 base = 0; base < total; base += 32u * kRelUnroll) {
+                if (base)
+                    fetch_flat(base);
+                u32 xo_[kRelUnroll], uo_[kRelUnroll], go_[kRelUnroll], fl_[kRelUnroll];
+                u64 old_[kRelUnroll];
+                bool has_[kRelUnroll];
+#pragma unroll
+                for (int j = 0; j < kRelUnroll; ++j) {
+                    xo_[j] = __shfl_sync(kFull, x, (int)ow_[j]);
+                    uo_[j] = __shfl_sync(kFull, u, (int)ow_[j]);
+                    go_[j] = __shfl_sync(kFull, gid, (int)ow_[j]);
+                    const int run_o = __shfl_sync(kFull, (int)run, (int)ow_[j]);   // every lane shuffles
+                    v_[j] = v_[j] && run_o != 0;
+                }
+#pragma unroll
+                for (int j = 0; j < kRelUnroll; ++j)
+                    old_[j] = v_[j] ? atomicAdd(&p.slots[s_[j]].W, ((u64)xo_[j] << 32) - 1ull) : 0ull;
+#pragma unroll
+                for (int j = 0; j < kRelUnroll; ++j) {
+                    fl_[j] = 0u;
                     has_[j] = v_[j] && (u32)old_[j] == 1u;
                     if (has_[j]) {
                         atomicAdd(&my_push[ow_[j]], 1u);
@@ -575,7 +727,7 @@ __global__ void sched_kernel(KParams p)
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                for (int j = 0; j < kRelUnroll; ++j) {
                     const u64 ent = ((u64)((u32)(old_[j] >> 32) + xo_[j]) << 32) | kStrongBit | (u64)s_[j];
                     stage(w, my_stage, ns, has_[j], ent, lane, st_spill);
                     if (fl_[j] & kInflight)
@@ -583,44 +735,78 @@ __global__ void sched_kernel(KParams p)
                 }
             }
         }
+        stage(w, my_stage, ns, c_has, ((u64)x << 32) | (u64)c_t, lane, st_spill);
+        if (c_fl & kInflight)
+            racy = gid;
         __syncwarp();
+        if (!per_lane) {
+            mp += my_push[lane];
+            keep_self = keep_self || my_keep[lane] != 0u;
+        }
 
         // ---- a race poisons the graph in which it was found
         if (racy != kEmpty32)
             atomicCAS(&p.descs[racy].status, 0, TG_ERR_RACE);
 
-        // ---- release own in-flight flags, then publish the staged activations
+        // ---- release own in-flight flags (with the new count and digest)
         if (race_check) {
-            if (run && my_keep[lane] == 0u)
-                p.slots[u].cnt = iter + 1u;
+            if (run)
+                __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt),
+                       make_uint2((iter + 1u) | (keep_self ? kInflight : 0u), dg));
             fence_acq_rel_gpu();
         }
-        publish(w, my_stage, ns, lane, st_spill);
-        __syncwarp();
-
-        // ---- settle the pending counts: + pushed - reserved - executed
+        if (run)
+            __stcs(&p.outv[u], x);
+        // ---- a warp whose step produced at most kHandMax activations runs
+        // them itself next (a chain never leaves the warp); wider output is
+        // published to the block's ring / public deque, where it merges with
+        // the siblings' work and spreads
         {
-            const u32 P = act ? my_push[lane] : 0u;
-            u32 rem = __ballot_sync(kFull, act);
-            while (rem) {
-                int l = __ffs(rem) - 1;
-                u32 g = __shfl_sync(kFull, gid, l);
-                bool in = act && gid == g;
-                u32 m = __ballot_sync(kFull, in);
-                u32 sumP = __reduce_add_sync(kFull, in ? P : 0u);
-                u32 sumU = __reduce_add_sync(kFull, in ? U : 0u);
-                if (lane == l) {
-                    const u32 E = (u32)__popc(m);
+            const u32 keep = ns <= kHandMax ? ns : 0u;
+            __syncwarp();
+            hand = (u32)lane < keep ? my_stage[lane] : kEmpty;
+            nh = (int)keep;
+            if (ns > keep)
+                publish(w, my_stage + keep, ns - keep, lane, st_spill);
+            __syncwarp();
+        }
+
+        // ---- settle the pending counts: + pushed - reserved - executed.
+        // The atomic's result is examined next iteration (settle_finish).
+        {
+            const u32 P = act ? mp : 0u;
+            if (single) {
+                const u32 E = (u32)__popc(__ballot_sync(kFull, act));
+                const u32 sumP = __reduce_add_sync(kFull, P);
+                const u32 sumU = __reduce_add_sync(kFull, U);
+                if (lane == 0 && E) {
                     const long long d = (long long)sumP - (long long)sumU - (long long)E;
-                    const u64 delta = ((u64)E << 32) + (u64)d;
-                    const u64 old = atomicAdd(&p.descs[g].pe, delta);
-                    const u64 nw = old + delta;
-                    if ((u32)(nw >> 32) > cap)
-                        atomicCAS(&p.descs[g].status, 0, TG_ERR_EXEC_LIMIT);
-                    if ((u32)nw == 0u)
-                        atomicSub(&p.ctl->graphs_left, 1u);
+                    pend_delta = ((u64)E << 32) + (u64)d;
+                    pend_old = atomicAdd(&p.descs[p.single_gid].pe, pend_delta);
+                    pend_g = p.single_gid;
+                    pend_cap = single_cap;
+                    pend = true;
                 }
-                rem &= ~m;
+            } else {
+                u32 rem = __ballot_sync(kFull, act);
+                while (rem) {
+                    int l = __ffs(rem) - 1;
+                    u32 g = __shfl_sync(kFull, gid, l);
+                    bool in = act && gid == g;
+                    u32 m = __ballot_sync(kFull, in);
+                    u32 sumP = __reduce_add_sync(kFull, in ? P : 0u);
+                    u32 sumU = __reduce_add_sync(kFull, in ? U : 0u);
+                    if (lane == l) {
+                        const u32 E = (u32)__popc(m);
+                        const long long d = (long long)sumP - (long long)sumU - (long long)E;
+                        pend_delta = ((u64)E << 32) + (u64)d;
+                        pend_old = atomicAdd(&p.descs[g].pe, pend_delta);
+                        pend_g = g;
+                        pend_cap = c_cap;
+                        pend = true;
+                    }
+                    rem &= ~m;
+                }
             }
         }
         if (w.err) {
@@ -644,6 +830,7 @@ __global__ void sched_kernel(KParams p)
         }
     }
 
+    settle_finish(p, pend, pend_old, pend_delta, pend_g, pend_cap);
     if (lane == 0) {
         atomicAdd(&s_stats[ST_POP_LOCAL], st_local);
         atomicAdd(&s_stats[ST_POP_OWN], st_own);
@@ -653,6 +840,7 @@ __global__ void sched_kernel(KParams p)
         atomicAdd(&s_stats[ST_SPILL], st_spill);
         atomicAdd(&s_stats[ST_IDLE], st_idle);
         atomicAdd(&s_stats[ST_ITERS], st_iters);
+        atomicAdd(&s_stats[ST_HAND], st_hand);
     }
     // tasks are counted per lane
     atomicAdd(&s_stats[ST_TASKS], st_tasks);
@@ -698,6 +886,8 @@ __global__ void rearm_kernel(KParams p)
             p.stats[i] = 0ull;
         for (u32 i = threadIdx.x; i < p.max_thieves; i += blockDim.x)
             p.thief_slots[i * 32u] = 0u;
+        for (u32 i = threadIdx.x; i < 32u; i += blockDim.x)
+            p.ctl->avail[i] = 0u;
         if (threadIdx.x == 0) {
             p.ctl->graphs_left = p.n_graphs;
             p.ctl->abort_code = 0;
