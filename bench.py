@@ -38,7 +38,12 @@ UNIT = "tasks/s"
 WORKLOAD = "large static DAGs, plain form: layered 1000x1000 (d~U{1..8}, R=16) + wavefront 1024x1024 (R=256)"
 
 
+SMALL = False   # --small: the same two shapes at reduced size (for profiler captures)
+
+
 def _graphs():
+    if SMALL:
+        return [w.config2a(levels=100, width=1000), w.config2b(side=256)]
     return [w.config2a(), w.config2b()]
 
 
@@ -152,7 +157,7 @@ def run_b300(args):
     execs_per_step = sum(g.n for g in graphs)   # static DAGs: every task runs once
     peaks, peak_kind = _peaks()
 
-    ex = Executor(arena_bytes=4 << 30)
+    ex = Executor(arena_bytes=(512 << 20) if SMALL else (4 << 30))
     handles = [ex.graph(g) for g in graphs]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = ex.stream
@@ -276,7 +281,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--small", action="store_true",
+                    help="layered 100x1000 + wavefront 256x256 (profiler captures; not a bench line)")
     args = ap.parse_args()
+    global SMALL
+    SMALL = args.small
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return
