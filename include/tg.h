@@ -170,6 +170,18 @@ int tg_batch_create(tg_ctx *ctx, tg_graph *const *gs, uint32_t n, tg_batch **out
 int tg_batch_launch(tg_ctx *ctx, tg_batch *b);
 int tg_batch_wait(tg_ctx *ctx, tg_batch *b, int *statuses);
 int tg_batch_destroy(tg_ctx *ctx, tg_batch *b);
+/* Autotune a batch (worker-block count, warps per block, deque depth, steal
+ * policy, victims per steal round, thief slots): time its launch under
+ * candidate geometries by coordinate descent, `trials` timed launches each,
+ * keep the fastest and re-capture the batch with it.  With cache_path
+ * non-NULL, a result cached for the same device and batch shape (graph,
+ * task, edge and source counts) is reused without searching; a new result is
+ * appended to the file.  The batch's graphs run during the search (their
+ * results are those of the last run).  *chosen and *best_ns may be NULL.
+ * TG_ERR_* of the first failing launch if a graph does not end TG_OK. */
+int tg_batch_autotune(tg_ctx *ctx, tg_batch *b, uint32_t trials, const char *cache_path,
+                      tg_ctx_opts *chosen, uint64_t *best_ns);
+
 /* Convenience: create, launch, wait and destroy; statuses may be NULL.
  * Returns TG_OK if every graph ended TG_OK, else the first error. */
 int tg_run_batch(tg_ctx *ctx, tg_graph *const *gs, uint32_t n, int *statuses);
@@ -191,6 +203,13 @@ typedef struct {
 } tg_stats;
 int tg_ctx_get_stats(tg_ctx *ctx, tg_stats *st);
 int tg_ctx_get_opts(const tg_ctx *ctx, tg_ctx_opts *opts);
+/* Change the launch geometry used by later single-graph launches and by
+ * batches created afterwards.  Reads worker_blocks, warps_per_block,
+ * deque_depth (at most the context's), steal_policy, max_steal, smem_ring,
+ * idle_sleep_ns and max_thieves (0 = default); other fields are ignored.
+ * TG_ERR_INVALID if a field is out of range or the block shape cannot be
+ * resident. */
+int tg_ctx_set_launch(tg_ctx *ctx, const tg_ctx_opts *launch);
 
 /* Roofline kernels (measurement only).
  *  tg_bench_payload: the task payload alone on `count` independent ids with

@@ -87,6 +87,9 @@ SIGNATURES = {
     "tg_run_batch": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
     "tg_ctx_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tg_stats)]),
     "tg_ctx_get_opts": (ctypes.c_int, [_vp, ctypes.POINTER(tg_ctx_opts)]),
+    "tg_ctx_set_launch": (ctypes.c_int, [_vp, ctypes.POINTER(tg_ctx_opts)]),
+    "tg_batch_autotune": (ctypes.c_int, [_vp, _vp, _u32, ctypes.c_char_p, ctypes.POINTER(tg_ctx_opts),
+                                         ctypes.POINTER(_u64)]),
     "tg_bench_payload": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "tg_bench_atomics": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(_u64)]),
     "tg_run_noalloc": (ctypes.c_int, [_u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]),
@@ -233,6 +236,22 @@ def tg_ctx_get_opts(ctx) -> dict:
     o = tg_ctx_opts()
     _check(load().tg_ctx_get_opts(_vp(ctx), ctypes.byref(o)), "tg_ctx_get_opts")
     return {k: getattr(o, k) for k, _ in o._fields_}
+
+
+def tg_ctx_set_launch(ctx, **fields) -> int:
+    o = tg_ctx_opts()
+    for k, v in fields.items():
+        setattr(o, k, v)
+    return load().tg_ctx_set_launch(_vp(ctx), ctypes.byref(o))
+
+
+def tg_batch_autotune(ctx, b, trials=2, cache_path=None):
+    """Returns (status, chosen options dict, best device ns)."""
+    o = tg_ctx_opts()
+    t = _u64(0)
+    st = load().tg_batch_autotune(_vp(ctx), _vp(b), trials, cache_path.encode() if cache_path else None,
+                                  ctypes.byref(o), ctypes.byref(t))
+    return st, {k: getattr(o, k) for k, _ in o._fields_}, t.value
 
 
 def tg_bench_payload(ctx, count, rounds):

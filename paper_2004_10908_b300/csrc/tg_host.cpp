@@ -3,7 +3,9 @@
 // source set of Algorithm 8), launches, batches and tickets.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <map>
 #include <new>
 #include <vector>
@@ -17,6 +19,14 @@ namespace {
 
 constexpr u32 kMaxGraphs = 1u << 16;
 constexpr u32 kMaxDegree = 0xFFFFu;
+constexpr int kMaxBlocks = 1024;   // per-block structures are allocated for this many blocks
+
+// Launch geometry of the persistent scheduler: chosen per launch (a batch
+// keeps the one it was captured with), within what the context allocated.
+struct Geometry {
+    int blocks = 0, threads = 0;
+    u32 ring = 0, depth = 0, policy = 0, max_steal = 0, thieves = 0, idle_ns = 0;
+};
 
 u64 now_ns()
 {
@@ -101,6 +111,8 @@ struct tg_batch {
     tg_ctx *ctx = nullptr;
     std::vector<tg_graph *> gs;
     u64 lt_off = 0, lt_len = 0;
+    u32 max_n = 0, total_src = 0;
+    Geometry geo;
     KParams kp{};
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;
@@ -139,8 +151,9 @@ struct tg_ctx {
     std::vector<u32> free_gids;
     u64 budget = 0, used = 0;
 
-    int nblocks = 0, threads = 0;
-    u32 smem_entries = 0, dq_depth = 0;
+    Geometry geo;        // geometry of single-graph launches
+    u32 dq_cap = 0;      // entries allocated per block deque
+    Geometry last_geo;   // geometry of the last scheduler launch (statistics)
 
     u32 *h_cancel = nullptr, *d_cancel = nullptr;
     i32 *h_status = nullptr, *d_status = nullptr;
@@ -163,7 +176,7 @@ namespace {
             return TG_ERR_CUDA;             \
     } while (0)
 
-KParams base_params(tg_ctx *c)
+KParams base_params(tg_ctx *c, const Geometry &g)
 {
     KParams p{};
     p.slots = c->slots;
@@ -175,17 +188,18 @@ KParams base_params(tg_ctx *c)
     p.stats = c->stats;
     p.inj = c->inj;
     p.inj_mask = (u32)(c->inj_cap - 1);
-    p.nblocks = (u32)c->nblocks;
+    p.nblocks = (u32)g.blocks;
     p.dq = c->dq;
     p.dqc = c->dqc;
-    p.dq_mask = c->dq_depth - 1u;
-    p.smem_mask = c->smem_entries - 1u;
+    p.dq_mask = g.depth - 1u;
+    p.dq_stride = c->dq_cap;
+    p.smem_mask = g.ring - 1u;
     p.flags = c->opts.flags;
-    p.max_steal = (u32)c->opts.max_steal;
-    p.steal_policy = (u32)c->opts.steal_policy;
+    p.max_steal = g.max_steal;
+    p.steal_policy = g.policy;
     p.node_cap = (u32)c->node_cap;
-    p.idle_sleep_ns = c->opts.idle_sleep_ns;
-    p.max_thieves = (u32)c->opts.max_thieves;
+    p.idle_sleep_ns = g.idle_ns;
+    p.max_thieves = g.thieves;
     p.thief_slots = c->thief_slots;
     p.time_limit_ns = c->opts.time_limit_ns;
     p.cancel = c->d_cancel;
@@ -232,9 +246,47 @@ int clear_if_dirty(tg_ctx *c)
     if (!c->dirty)
         return TG_OK;
     TG_CUDA(launch_clear(c->inj, c->inj_cap, c->stream));
-    TG_CUDA(launch_clear(c->dq, (size_t)c->nblocks * c->dq_depth, c->stream));
+    TG_CUDA(launch_clear(c->dq, (size_t)kMaxBlocks * c->dq_cap, c->stream));
     c->dirty = false;
     return TG_OK;
+}
+
+// Validate the launch fields of `o` (0 = default) and size the grid from the
+// occupancy of the scheduler kernel at that block shape.
+int resolve_geometry(const tg_ctx *c, const tg_ctx_opts &o, Geometry &g)
+{
+    const int warps = o.warps_per_block > 0 ? o.warps_per_block : 8;
+    const u32 ring = o.smem_ring > 0 ? (u32)o.smem_ring : 1024u;
+    const u32 depth = o.deque_depth > 0 ? (u32)o.deque_depth : c->dq_cap;
+    if (warps > 32 || !is_pow2(ring) || ring < 64 || ring > 8192 || !is_pow2(depth) || depth < 64 ||
+        depth > c->dq_cap || o.steal_policy < 0 || o.steal_policy > 1 || o.max_thieves > 1024 ||
+        o.max_steal < 0 || o.worker_blocks < 0)
+        return TG_ERR_INVALID;
+    int per_sm = 0;
+    if (sched_occupancy(warps * 32, sched_dyn_smem(ring, (u32)warps), &per_sm) != cudaSuccess || per_sm <= 0)
+        return TG_ERR_INVALID;   // this block shape cannot be resident
+    const int max_blocks = std::min(per_sm * c->sm_count, kMaxBlocks);
+    g.blocks = o.worker_blocks > 0 ? std::min(o.worker_blocks, max_blocks) : max_blocks;
+    g.threads = warps * 32;
+    g.ring = ring;
+    g.depth = depth;
+    g.policy = (u32)o.steal_policy;
+    g.max_steal = o.max_steal > 0 ? (u32)o.max_steal : 8u;
+    g.thieves = o.max_thieves > 0 ? (u32)o.max_thieves : 16u;
+    g.idle_ns = o.idle_sleep_ns > 0 ? o.idle_sleep_ns : 256u;
+    return TG_OK;
+}
+
+void geometry_to_opts(const Geometry &g, tg_ctx_opts &o)
+{
+    o.worker_blocks = g.blocks;
+    o.warps_per_block = g.threads / 32;
+    o.deque_depth = (int32_t)g.depth;
+    o.steal_policy = (int32_t)g.policy;
+    o.max_steal = (int32_t)g.max_steal;
+    o.smem_ring = (int32_t)g.ring;
+    o.max_thieves = (int32_t)g.thieves;
+    o.idle_sleep_ns = g.idle_ns;
 }
 
 }  // namespace
@@ -273,31 +325,9 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
     if (opts)
         c->opts = *opts;
     tg_ctx_opts &o = c->opts;
-    if (o.warps_per_block <= 0)
-        o.warps_per_block = 8;
-    if (o.warps_per_block > 32) {
-        delete c;
-        return TG_ERR_INVALID;
-    }
     if (o.deque_depth <= 0)
         o.deque_depth = 4096;
-    if (o.smem_ring <= 0)
-        o.smem_ring = 1024;
-    if (!is_pow2((u64)o.deque_depth) || !is_pow2((u64)o.smem_ring) || o.smem_ring < 64 || o.deque_depth < 64) {
-        delete c;
-        return TG_ERR_INVALID;
-    }
-    if (o.max_steal <= 0)
-        o.max_steal = 8;
-    if (o.idle_sleep_ns == 0)
-        o.idle_sleep_ns = 256;
-    if (o.max_thieves <= 0)
-        o.max_thieves = 16;
-    if (o.max_thieves > 1024) {
-        delete c;
-        return TG_ERR_INVALID;
-    }
-    if (o.steal_policy < 0 || o.steal_policy > 1) {
+    if (!is_pow2((u64)o.deque_depth) || o.deque_depth < 64 || o.deque_depth > (1 << 20)) {
         delete c;
         return TG_ERR_INVALID;
     }
@@ -314,17 +344,13 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
         delete c;
         return TG_ERR_CUDA;
     }
-    c->threads = o.warps_per_block * 32;
-    c->smem_entries = (u32)o.smem_ring;
-    c->dq_depth = (u32)o.deque_depth;
-    int per_sm = 0;
-    if (sched_occupancy(c->threads, sched_dyn_smem(c->smem_entries, (u32)o.warps_per_block), &per_sm) != cudaSuccess || per_sm <= 0) {
+    c->dq_cap = (u32)o.deque_depth;
+    int rg = resolve_geometry(c, o, c->geo);
+    if (rg != TG_OK) {
         delete c;
-        return TG_ERR_CUDA;
+        return rg;
     }
-    int max_blocks = std::min(per_sm * c->sm_count, 1024);   // work-available bitmap size
-    c->nblocks = o.worker_blocks > 0 ? std::min(o.worker_blocks, max_blocks) : max_blocks;
-    o.worker_blocks = c->nblocks;
+    geometry_to_opts(c->geo, o);
 
     // ---- carve the arena
     size_t off = 0;
@@ -335,12 +361,12 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
         return p;
     };
     c->ctl = (LaunchCtl *)take(sizeof(LaunchCtl));
-    c->stats = (u64 *)take((size_t)c->nblocks * ST_COUNT * sizeof(u64));
+    c->stats = (u64 *)take((size_t)kMaxBlocks * ST_COUNT * sizeof(u64));
     c->scratch = (u32 *)take(4096);
     c->thief_slots = (u32 *)take((size_t)1024 * 128);
     c->descs = (GDesc *)take((size_t)kMaxGraphs * sizeof(GDesc));
-    c->dqc = (QCtr *)take((size_t)c->nblocks * sizeof(QCtr));
-    c->dq = (u64 *)take((size_t)c->nblocks * c->dq_depth * sizeof(u64));
+    c->dqc = (QCtr *)take((size_t)kMaxBlocks * sizeof(QCtr));
+    c->dq = (u64 *)take((size_t)kMaxBlocks * c->dq_cap * sizeof(u64));
     off = (off + 255) & ~(size_t)255;
     if (off >= arena_bytes) {
         delete c;
@@ -434,6 +460,19 @@ int tg_ctx_destroy(tg_ctx *c)
     if (c->ev_k1)
         cudaEventDestroy(c->ev_k1);
     delete c;
+    return TG_OK;
+}
+
+int tg_ctx_set_launch(tg_ctx *c, const tg_ctx_opts *launch)
+{
+    if (!c || !launch)
+        return TG_ERR_INVALID;
+    Geometry g;
+    int rc = resolve_geometry(c, *launch, g);
+    if (rc != TG_OK)
+        return rc;
+    c->geo = g;
+    geometry_to_opts(g, c->opts);
     return TG_OK;
 }
 
@@ -634,7 +673,7 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     int rc = clear_if_dirty(c);
     if (rc != TG_OK)
         return rc;
-    KParams p = base_params(c);
+    KParams p = base_params(c, c->geo);
     p.lt = nullptr;
     p.n_graphs = 1;
     p.single_gid = g->gid;
@@ -645,10 +684,11 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     TG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
     TG_CUDA(launch_rearm(p, c->stream));
     TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
-    TG_CUDA(launch_sched(p, c->nblocks, c->threads, c->stream));
+    TG_CUDA(launch_sched(p, c->geo.blocks, c->geo.threads, c->stream));
     TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
     TG_CUDA(launch_finalize(p, c->stream));
     TG_CUDA(cudaEventRecord(s.ev, c->stream));
+    c->last_geo = c->geo;
     c->timed = true;
     g->busy = s.ev;
     *ticket = c->next_ticket++;
@@ -750,6 +790,43 @@ int tg_result_copy(tg_ctx *c, const tg_graph *g, uint32_t *out, uint32_t *cnt, u
     return TG_OK;
 }
 
+}  // extern "C"
+
+// (Re)capture re-arm + scheduler + finalize of a batch with its geometry as
+// one CUDA graph; replays reuse it.
+static int batch_capture(tg_ctx *c, tg_batch *b)
+{
+    KParams p = base_params(c, b->geo);
+    p.lt = (const LEntry *)(c->edges + b->lt_off);
+    p.n_graphs = (u32)b->gs.size();
+    p.single_gid = 0;
+    p.max_n = b->max_n;
+    p.total_sources = b->total_src;
+    b->kp = p;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cs = c->capture_stream;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return TG_ERR_CUDA;
+    cudaError_t e1 = launch_rearm(p, cs);
+    cudaError_t e2 = launch_sched(p, b->geo.blocks, b->geo.threads, cs);
+    cudaError_t e3 = launch_finalize(p, cs);
+    cudaError_t e4 = cudaStreamEndCapture(cs, &graph);
+    if (e1 || e2 || e3 || e4 || !graph) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return TG_ERR_CUDA;
+    }
+    cudaError_t e5 = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    return e5 == cudaSuccess ? TG_OK : TG_ERR_CUDA;
+}
+
+extern "C" {
+
 int tg_batch_create(tg_ctx *c, tg_graph *const *gs, uint32_t n, tg_batch **out)
 {
     if (!c || !gs || !out || n == 0 || n > kMaxGraphs)
@@ -786,33 +863,15 @@ int tg_batch_create(tg_ctx *c, tg_graph *const *gs, uint32_t n, tg_batch **out)
         tg_batch_destroy(c, b);
         return TG_ERR_CUDA;
     }
-    KParams p = base_params(c);
-    p.lt = (const LEntry *)(c->edges + b->lt_off);
-    p.n_graphs = n;
-    p.single_gid = 0;
-    p.max_n = max_n;
-    p.total_sources = (u32)inj;
-    b->kp = p;
-    // capture re-arm + scheduler + finalize once; replays reuse it
-    cudaGraph_t graph = nullptr;
-    cudaStream_t cs = c->capture_stream;
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    b->max_n = max_n;
+    b->total_src = (u32)inj;
+    b->geo = c->geo;
+    int rc = batch_capture(c, b);
+    if (rc != TG_OK) {
         tg_batch_destroy(c, b);
-        return TG_ERR_CUDA;
+        return rc;
     }
-    cudaError_t e1 = launch_rearm(p, cs);
-    cudaError_t e2 = launch_sched(p, c->nblocks, c->threads, cs);
-    cudaError_t e3 = launch_finalize(p, cs);
-    cudaError_t e4 = cudaStreamEndCapture(cs, &graph);
-    if (e1 || e2 || e3 || e4 || !graph) {
-        if (graph)
-            cudaGraphDestroy(graph);
-        tg_batch_destroy(c, b);
-        return TG_ERR_CUDA;
-    }
-    cudaError_t e5 = cudaGraphInstantiate(&b->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e5 != cudaSuccess || cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
         tg_batch_destroy(c, b);
         return TG_ERR_CUDA;
     }
@@ -835,6 +894,7 @@ int tg_batch_launch(tg_ctx *c, tg_batch *b)
     TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
     TG_CUDA(cudaEventRecord(b->done, c->stream));
     c->timed = true;
+    c->last_geo = b->geo;
     for (tg_graph *g : b->gs)
         g->busy = b->done;
     b->launched = true;
@@ -881,6 +941,175 @@ int tg_batch_destroy(tg_ctx *c, tg_batch *b)
     return TG_OK;
 }
 
+}  // extern "C"
+
+// One timed replay of a batch under its current geometry (graph re-captured
+// by the caller); returns the device time or 0 on failure, *status the
+// first graph error.
+static u64 batch_time(tg_ctx *c, tg_batch *b, int *status)
+{
+    if (tg_batch_launch(c, b) != TG_OK) {
+        *status = TG_ERR_CUDA;
+        return 0;
+    }
+    *status = tg_batch_wait(c, b, nullptr);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1) != cudaSuccess)
+        return 0;
+    return (u64)((double)ms * 1e6);
+}
+
+static std::string batch_key(tg_ctx *c, tg_batch *b)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, c->device);
+    u64 nodes = 0, edges = 0, srcs = 0;
+    for (tg_graph *g : b->gs) {
+        nodes += g->n;
+        edges += g->m;
+        srcs += g->n_src;
+    }
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s|sm%d|flags%u|g%zu|n%llu|m%llu|s%llu", prop.name, c->sm_count,
+                  c->opts.flags, b->gs.size(), (unsigned long long)nodes, (unsigned long long)edges,
+                  (unsigned long long)srcs);
+    std::string k(buf);
+    for (char &ch : k)
+        if (ch == '\t' || ch == '\n')
+            ch = ' ';
+    return k;
+}
+
+extern "C" {
+
+int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache_path, tg_ctx_opts *chosen,
+                      uint64_t *best_ns)
+{
+    if (!c || !b || b->ctx != c)
+        return TG_ERR_INVALID;
+    if (trials == 0)
+        trials = 2;
+    const std::string key = batch_key(c, b);
+    tg_ctx_opts best{};
+    geometry_to_opts(b->geo, best);
+    u64 best_t = 0;
+    bool cached = false;
+    if (cache_path) {
+        if (FILE *f = std::fopen(cache_path, "r")) {
+            char line[1024];
+            while (std::fgets(line, sizeof(line), f)) {
+                char *tab = std::strchr(line, '\t');
+                if (!tab || std::string(line, tab) != key)
+                    continue;
+                tg_ctx_opts o{};
+                unsigned long long t = 0;
+                if (std::sscanf(tab + 1, "%d %d %d %d %d %d %d %u %llu", &o.worker_blocks, &o.warps_per_block,
+                                &o.deque_depth, &o.steal_policy, &o.max_steal, &o.max_thieves, &o.smem_ring,
+                                &o.idle_sleep_ns, &t) == 9) {
+                    Geometry g;
+                    if (resolve_geometry(c, o, g) == TG_OK) {
+                        best = o;
+                        best_t = t;
+                        cached = true;
+                    }
+                }
+            }
+            std::fclose(f);
+        }
+    }
+    int status = TG_OK;
+    auto measure = [&](const tg_ctx_opts &o, u64 &t_out) -> int {
+        Geometry g;
+        int rc = resolve_geometry(c, o, g);
+        if (rc != TG_OK)
+            return rc;
+        b->geo = g;
+        rc = batch_capture(c, b);
+        if (rc != TG_OK)
+            return rc;
+        int st = TG_OK;
+        batch_time(c, b, &st);   // warm-up replay
+        if (st != TG_OK)
+            return st;
+        u64 tmin = 0;
+        for (uint32_t i = 0; i < trials; ++i) {
+            u64 t = batch_time(c, b, &st);
+            if (st != TG_OK)
+                return st;
+            if (t && (tmin == 0 || t < tmin))
+                tmin = t;
+        }
+        t_out = tmin;
+        return TG_OK;
+    };
+    if (!cached) {
+        int rc = measure(best, best_t);
+        if (rc != TG_OK)
+            return rc;
+        const int warps_c[] = {4, 8, 16};
+        const int bpsm_c[] = {1, 2, 4};
+        const int depth_c[] = {(int)std::max<u32>(64u, c->dq_cap / 4u), (int)c->dq_cap};
+        const int policy_c[] = {0, 1};
+        const int steal_c[] = {2, 8, 32};
+        const int thief_c[] = {8, 16, 64};
+        auto try_knob = [&](auto setter, const int *vals, int nv) -> int {
+            for (int i = 0; i < nv; ++i) {
+                tg_ctx_opts o = best;
+                setter(o, vals[i]);
+                Geometry g;
+                if (resolve_geometry(c, o, g) != TG_OK)
+                    continue;
+                geometry_to_opts(g, o);
+                if (std::memcmp(&o, &best, sizeof(o)) == 0)
+                    continue;
+                u64 t = 0;
+                int rc = measure(o, t);
+                if (rc == TG_ERR_INVALID || rc == TG_ERR_CUDA)
+                    continue;
+                if (rc != TG_OK)
+                    return rc;
+                if (t && t < best_t) {
+                    best_t = t;
+                    best = o;
+                }
+            }
+            return TG_OK;
+        };
+        int rc2 = TG_OK;
+        if ((rc2 = try_knob([](tg_ctx_opts &o, int v) { o.warps_per_block = v; o.worker_blocks = 0; }, warps_c, 3)) != TG_OK ||
+            (rc2 = try_knob([&](tg_ctx_opts &o, int v) { o.worker_blocks = v * c->sm_count; }, bpsm_c, 3)) != TG_OK ||
+            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.deque_depth = v; }, depth_c, 2)) != TG_OK ||
+            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.steal_policy = v; }, policy_c, 2)) != TG_OK ||
+            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.max_steal = v; }, steal_c, 3)) != TG_OK ||
+            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.max_thieves = v; }, thief_c, 3)) != TG_OK)
+            return rc2;
+        if (cache_path) {
+            if (FILE *f = std::fopen(cache_path, "a")) {
+                std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %llu\n", key.c_str(), best.worker_blocks,
+                             best.warps_per_block, best.deque_depth, best.steal_policy, best.max_steal,
+                             best.max_thieves, best.smem_ring, best.idle_sleep_ns, (unsigned long long)best_t);
+                std::fclose(f);
+            }
+        }
+    }
+    Geometry g;
+    int rc = resolve_geometry(c, best, g);
+    if (rc != TG_OK)
+        return rc;
+    b->geo = g;
+    rc = batch_capture(c, b);
+    if (rc != TG_OK)
+        return rc;
+    (void)status;
+    if (chosen) {
+        *chosen = c->opts;
+        geometry_to_opts(g, *chosen);
+    }
+    if (best_ns)
+        *best_ns = best_t;
+    return TG_OK;
+}
+
 int tg_run_batch(tg_ctx *c, tg_graph *const *gs, uint32_t n, int *statuses)
 {
     tg_batch *b = nullptr;
@@ -900,9 +1129,11 @@ int tg_ctx_get_stats(tg_ctx *c, tg_stats *st)
         return TG_ERR_INVALID;
     memset(st, 0, sizeof(*st));
     TG_CUDA(cudaStreamSynchronize(c->stream));
-    std::vector<u64> h((size_t)c->nblocks * ST_COUNT);
+    const Geometry &lg = c->last_geo.blocks > 0 ? c->last_geo : c->geo;
+    const int nb = lg.blocks;
+    std::vector<u64> h((size_t)nb * ST_COUNT);
     TG_CUDA(cudaMemcpy(h.data(), c->stats, h.size() * sizeof(u64), cudaMemcpyDeviceToHost));
-    for (int b = 0; b < c->nblocks; ++b) {
+    for (int b = 0; b < nb; ++b) {
         const u64 *s = &h[(size_t)b * ST_COUNT];
         st->tasks += s[ST_TASKS];
         st->pops_local += s[ST_POP_LOCAL];
@@ -920,8 +1151,8 @@ int tg_ctx_get_stats(tg_ctx *c, tg_stats *st)
         if (cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1) == cudaSuccess)
             st->kernel_ns = (u64)((double)ms * 1e6);
     }
-    st->worker_blocks = (u32)c->nblocks;
-    st->warps_per_block = (u32)c->opts.warps_per_block;
+    st->worker_blocks = (u32)nb;
+    st->warps_per_block = (u32)(lg.threads / 32);
     return TG_OK;
 }
 

@@ -104,6 +104,8 @@ struct KParams {
     u32 node_cap;          // node pool size: a popped entry beyond it is a scheduler fault
     u32 idle_sleep_ns;     // wait of a non-thief idle warp
     u32 max_thieves;       // thief slots (blocks stealing / polling at once)
+    u32 dq_stride;         // entries allocated per block deque (>= dq_mask + 1)
+    u32 pad3;
     u32 *thief_slots;      // max_thieves words, each on its own 128-byte line
     u64 time_limit_ns;
     volatile u32 *cancel;  // host-mapped cancel flag (may be null)

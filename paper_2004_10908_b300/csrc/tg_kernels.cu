@@ -325,7 +325,7 @@ __global__ void sched_kernel(KParams p)
     WarpCtx w;
     w.local = Ring{&s_head, &s_tail, s_ring, p.smem_mask};
     w.own = Ring{&p.dqc[blockIdx.x].head, &p.dqc[blockIdx.x].tail,
-                 p.dq + (size_t)blockIdx.x * (p.dq_mask + 1u), p.dq_mask};
+                 p.dq + (size_t)blockIdx.x * p.dq_stride, p.dq_mask};
     w.inj = Ring{&p.ctl->inj.head, &p.ctl->inj.tail, p.inj, p.inj_mask};
     // keep locally what the block's warps can take at once; beyond that,
     // new activations go to the public deque where other blocks steal them
@@ -346,6 +346,7 @@ __global__ void sched_kernel(KParams p)
     u32 backoff = 256;
     const u32 my_slot = blockIdx.x % p.max_thieves;
     u32 idle = 0;
+    u32 noslot = 0;
     // activations this warp kept for itself (lanes [0, nh) of `hand`)
     u64 hand = kEmpty;
     int nh = 0;
@@ -385,6 +386,23 @@ __global__ void sched_kernel(KParams p)
                 am = __shfl_sync(kFull, am, 0);
                 if (am != 1) {
                     st_idle++;
+                    if (am == 2) {
+                        // no thief slot: still notice the end of the launch, at a
+                        // low rate (one read per block every few microseconds)
+                        int stop = 0;
+                        if (lane == 0 && ((++noslot & 3u) == 0u)) {
+                            if (vld32(&p.ctl->graphs_left) == 0u || vldi(&p.ctl->abort_code) != 0) {
+                                stop = 1;
+                            } else if (globaltimer() > deadline) {
+                                atomicCAS(&p.ctl->abort_code, 0, TG_ERR_TIMEOUT);
+                                stop = 1;
+                            }
+                            if (stop)
+                                *(volatile int *)&s_stop = 1;
+                        }
+                        if (__shfl_sync(kFull, stop, 0))
+                            break;
+                    }
                     __nanosleep(am == 2 ? backoff : p.idle_sleep_ns);
                     if (am == 2)
                         backoff = min(backoff * 2u, 4096u);
@@ -425,7 +443,7 @@ __global__ void sched_kernel(KParams p)
                                 bits &= bits - 1u;
                                 if (v >= p.nblocks)
                                     break;
-                                Ring vr{&p.dqc[v].head, &p.dqc[v].tail, p.dq + (size_t)v * (p.dq_mask + 1u),
+                                Ring vr{&p.dqc[v].head, &p.dqc[v].tail, p.dq + (size_t)v * p.dq_stride,
                                         p.dq_mask};
                                 st_try++;
                                 tries++;

@@ -33,6 +33,13 @@ class Batch:
     def wait(self):
         return B.tg_batch_wait(self.ex.ctx, self.handle, len(self.graphs))
 
+    def autotune(self, trials=2, cache_path=None):
+        """Pick and apply the fastest launch geometry (see tg_batch_autotune)."""
+        st, chosen, ns = B.tg_batch_autotune(self.ex.ctx, self.handle, trials, cache_path)
+        if st != B.TG_OK:
+            raise B.TgError(st, "tg_batch_autotune")
+        return chosen, ns
+
     def destroy(self):
         if self.handle:
             B.tg_batch_destroy(self.ex.ctx, self.handle)
@@ -108,6 +115,11 @@ class Executor:
 
     def opts(self) -> dict:
         return B.tg_ctx_get_opts(self.ctx)
+
+    def set_launch(self, **fields):
+        st = B.tg_ctx_set_launch(self.ctx, **fields)
+        if st != B.TG_OK:
+            raise B.TgError(st, "tg_ctx_set_launch")
 
     def bench_payload(self, count, rounds):
         return B.tg_bench_payload(self.ctx, count, rounds)
