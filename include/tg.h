@@ -151,6 +151,43 @@ int tg_poll(tg_ctx *ctx, uint64_t ticket);
 /* Blocks until the submission finished; returns its status. */
 int tg_wait(tg_ctx *ctx, uint64_t ticket);
 
+/* Make another execution instance of graph g: its own task state, outputs
+ * and graph slot, sharing g's packed successor lists (no host packing, no
+ * kernel: copy-engine copies on a side stream).  Several instances of one
+ * graph may run at the same time.  Destroy it with tg_graph_destroy; g cannot
+ * be destroyed while it has instances (TG_ERR_BUSY).  TG_ERR_BUDGET if the
+ * memory budget or the pools cannot hold it. */
+int tg_instance_create(tg_ctx *ctx, tg_graph *g, tg_graph **out);
+
+/* Serving (continuous batching): start a resident scheduler on the context
+ * stream.  While it runs, tg_submit queues a graph (or instance) through a
+ * device submission ring -- its task state is re-armed by a copy-engine copy
+ * and the resident kernel injects its sources while other graphs are running
+ * -- and tg_poll / tg_wait read the completion records the kernel posts to
+ * host-mapped memory.  tg_run and batches return TG_ERR_BUSY meanwhile.
+ * time_limit_ns bounds the server's lifetime (0 = 60 s); a graph still in
+ * flight at the limit ends with TG_ERR_TIMEOUT.  Admission by memory budget
+ * is the caller's loop: tg_instance_create / tg_graph_create fail with
+ * TG_ERR_BUDGET until finished graphs are destroyed. */
+int tg_serve_start(tg_ctx *ctx, uint64_t time_limit_ns);
+/* Stop the resident scheduler and wait for it; returns TG_OK or the code
+ * that ended it (TG_ERR_TIMEOUT, TG_ERR_INTERNAL). */
+int tg_serve_stop(tg_ctx *ctx);
+
+/* Request loop over a running server: request i arrives arrival_ns[i] after
+ * the call starts (ascending) and asks for one execution of
+ * templates[which[i]].  It is admitted as soon as an instance fits the
+ * memory budget and a graph slot is free (FIFO otherwise), submitted while
+ * other requests run, and its instance is destroyed the moment it finishes,
+ * freeing budget for waiting requests.  Per request: latency_ns[i] = finish
+ * minus arrival on the host clock, status[i].  *max_in_flight (nullable)
+ * receives the most requests on the device at once.  keep (nullable, n
+ * entries) receives each finished instance instead of destroying it (the
+ * caller destroys them).  Returns TG_OK or the first request's error. */
+int tg_serve_replay(tg_ctx *ctx, tg_graph *const *templates, uint32_t n_templates, const uint32_t *which,
+                    const uint64_t *arrival_ns, uint32_t n_requests, uint64_t *latency_ns, int *status,
+                    uint32_t *max_in_flight, tg_graph **keep);
+
 /* Ask the device to stop: running graphs end with TG_ERR_CANCELLED (the
  * workers poll a host-mapped flag; the flag is cleared at the next launch). */
 int tg_cancel(tg_ctx *ctx);

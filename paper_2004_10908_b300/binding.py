@@ -88,6 +88,10 @@ SIGNATURES = {
     "tg_ctx_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tg_stats)]),
     "tg_ctx_get_opts": (ctypes.c_int, [_vp, ctypes.POINTER(tg_ctx_opts)]),
     "tg_ctx_set_launch": (ctypes.c_int, [_vp, ctypes.POINTER(tg_ctx_opts)]),
+    "tg_instance_create": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "tg_serve_start": (ctypes.c_int, [_vp, _u64]),
+    "tg_serve_stop": (ctypes.c_int, [_vp]),
+    "tg_serve_replay": (ctypes.c_int, [_vp, _vp, _u32, _vp, _vp, _u32, _vp, _vp, ctypes.POINTER(_u32), _vp]),
     "tg_batch_autotune": (ctypes.c_int, [_vp, _vp, _u32, ctypes.c_char_p, ctypes.POINTER(tg_ctx_opts),
                                          ctypes.POINTER(_u64)]),
     "tg_bench_payload": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
@@ -236,6 +240,36 @@ def tg_ctx_get_opts(ctx) -> dict:
     o = tg_ctx_opts()
     _check(load().tg_ctx_get_opts(_vp(ctx), ctypes.byref(o)), "tg_ctx_get_opts")
     return {k: getattr(o, k) for k, _ in o._fields_}
+
+
+def tg_instance_create(ctx, g):
+    out = _vp()
+    st = load().tg_instance_create(_vp(ctx), _vp(g), ctypes.byref(out))
+    return st, (out.value if st == TG_OK else None)
+
+
+def tg_serve_start(ctx, time_limit_ns=0) -> int:
+    return load().tg_serve_start(_vp(ctx), time_limit_ns)
+
+
+def tg_serve_stop(ctx) -> int:
+    return load().tg_serve_stop(_vp(ctx))
+
+
+def tg_serve_replay(ctx, templates, which, arrival_ns, keep=False):
+    """Returns (status, latency_ns[], status[], max_in_flight, kept instance handles or None)."""
+    which = np.ascontiguousarray(which, dtype=np.uint32)
+    arrival = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+    n = which.shape[0]
+    lat = np.zeros(n, np.uint64)
+    sts = np.zeros(n, np.int32)
+    peak = _u32(0)
+    kept = (_vp * n)() if keep else None
+    st = load().tg_serve_replay(_vp(ctx), ctypes.cast(_handles(templates), _vp), len(templates),
+                                which.ctypes.data_as(_vp), arrival.ctypes.data_as(_vp), n,
+                                lat.ctypes.data_as(_vp), sts.ctypes.data_as(_vp), ctypes.byref(peak),
+                                ctypes.cast(kept, _vp) if keep else None)
+    return st, lat, sts, peak.value, ([kept[i] for i in range(n)] if keep else None)
 
 
 def tg_ctx_set_launch(ctx, **fields) -> int:

@@ -20,6 +20,7 @@ namespace {
 constexpr u32 kMaxGraphs = 1u << 16;
 constexpr u32 kMaxDegree = 0xFFFFu;
 constexpr int kMaxBlocks = 1024;   // per-block structures are allocated for this many blocks
+constexpr u32 kSubRing = 1u << 16;  // server-mode submission / completion ring entries
 
 // Launch geometry of the persistent scheduler: chosen per launch (a batch
 // keeps the one it was captured with), within what the context allocated.
@@ -97,14 +98,26 @@ struct RangeAlloc {
 
 }  // namespace
 
+// A graph owns its packed form in the edge pool -- successor lists (graph-
+// local ids), the source list and a pristine image of its 32-byte task
+// records -- and an execution instance: a chunk-aligned range of the node
+// pool (task records + join/execution state + outputs) and a descriptor
+// slot (gid).  An instance made by tg_instance_create shares its template's
+// packed form and owns only an execution range and a gid.
 struct tg_graph {
     tg_ctx *ctx = nullptr;
+    tg_graph *tmpl = nullptr;     // the graph whose packed form this instance uses
+    int n_inst = 0;               // live instances made from this graph
     u32 gid = 0;
     u32 n = 0, m = 0, n_src = 0, n_cond = 0;
-    u64 node_off = 0, edge_off = 0, edge_len = 0;
+    u64 node_off = 0, chunk_off = 0, n_chunks = 0;
+    u64 edge_off = 0, edge_len = 0, pristine_off = 0;
     u32 seed = 0;
     u64 pack_ns = 0, upload_ns = 0, bytes = 0;
     cudaEvent_t busy = nullptr;   // event of the launch it is in (null: idle)
+    cudaEvent_t ready = nullptr;  // instance set-up copies (null: nothing to wait for)
+    u64 serve_ticket = 0;         // server mode: ticket of the submission in flight
+    bool setup_pending = false;   // an instance whose descriptor / chunk table are not written yet
 };
 
 struct tg_batch {
@@ -143,8 +156,18 @@ struct tg_ctx {
     u32 *thief_slots = nullptr;
     NodeSlot *slots = nullptr;
     u32 *outv = nullptr;
-    u32 *gidv = nullptr;
+    u32 *chunk_gid = nullptr;
     u32 *edges = nullptr;
+    cudaStream_t side = nullptr;   // instance set-up and server submissions
+    SubEntry *sub = nullptr;       // device submission ring
+    SubEntry *h_sub = nullptr;     // pinned staging of submission entries
+    u64 *h_comp = nullptr, *d_comp = nullptr;   // host-mapped completion ring
+    u32 *h_stop = nullptr, *d_stop = nullptr;   // host-mapped stop flag
+    u64 sub_seq = 0, comp_read = 0;
+    tg_graph **by_gid = nullptr;   // serving: graph in flight per gid
+    std::map<u64, int> serve_done; // serving: finished tickets -> status
+    std::vector<u64> newly_done;   // serving: tickets finished by the last drain
+    Geometry serve_geo;
 
     u64 node_cap = 0, edge_cap = 0, inj_cap = 0;
     RangeAlloc nodes, edge_pool;
@@ -161,6 +184,7 @@ struct tg_ctx {
     size_t stage_bytes = 0;
 
     bool dirty = true;   // queue slots may hold stale entries: clear before the next launch
+    bool serving = false; // a resident scheduler runs on the context stream
     u64 next_ticket = 1;
     std::map<u64, Submission> subs;
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
@@ -181,7 +205,7 @@ KParams base_params(tg_ctx *c, const Geometry &g)
     KParams p{};
     p.slots = c->slots;
     p.outv = c->outv;
-    p.gidv = c->gidv;
+    p.chunk_gid = c->chunk_gid;
     p.edges = c->edges;
     p.descs = c->descs;
     p.ctl = c->ctl;
@@ -204,6 +228,10 @@ KParams base_params(tg_ctx *c, const Geometry &g)
     p.time_limit_ns = c->opts.time_limit_ns;
     p.cancel = c->d_cancel;
     p.status_out = c->d_status;
+    p.sub = c->sub;
+    p.sub_mask = kSubRing - 1u;
+    p.comp_mask = kSubRing - 1u;
+    p.comp = c->d_comp;
     return p;
 }
 
@@ -364,6 +392,7 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
     c->stats = (u64 *)take((size_t)kMaxBlocks * ST_COUNT * sizeof(u64));
     c->scratch = (u32 *)take(4096);
     c->thief_slots = (u32 *)take((size_t)1024 * 128);
+    c->sub = (SubEntry *)take((size_t)kSubRing * sizeof(SubEntry));
     c->descs = (GDesc *)take((size_t)kMaxGraphs * sizeof(GDesc));
     c->dqc = (QCtr *)take((size_t)kMaxBlocks * sizeof(QCtr));
     c->dq = (u64 *)take((size_t)kMaxBlocks * c->dq_cap * sizeof(u64));
@@ -374,8 +403,11 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
     }
     size_t rest = arena_bytes - off - 4096;
     u64 ncap = o.max_nodes, ecap = o.max_edges;
+    ncap &= ~(u64)(kChunk - 1);
     if (ncap == 0) {
-        ncap = (rest / 96) & ~(u64)255;
+        // per task: 36 B execution range + 8 B of injection queue + 32 B
+        // pristine image + successors (about 8 x 4 B) in the edge pool
+        ncap = (rest / 128) & ~(u64)255;
         if (ncap > kMaxNodeIndex)
             ncap = kMaxNodeIndex & ~(u64)255;
     }
@@ -398,7 +430,7 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
     c->inj = (u64 *)take((size_t)icap * 8);
     c->slots = (NodeSlot *)take((size_t)ncap * sizeof(NodeSlot));
     c->outv = (u32 *)take((size_t)ncap * 4);
-    c->gidv = (u32 *)take((size_t)ncap * 4);
+    c->chunk_gid = (u32 *)take((size_t)(ncap >> kChunkShift) * 4 + 256);
     c->edges = (u32 *)take((size_t)ecap * 4);
     if (off > arena_bytes) {
         delete c;
@@ -407,9 +439,9 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
     c->node_cap = ncap;
     c->edge_cap = ecap;
     c->inj_cap = icap;
-    c->nodes.init(ncap);
+    c->nodes.init(ncap >> kChunkShift);   // allocated in 256-task chunks
     c->edge_pool.init(ecap);
-    c->budget = o.mem_budget_bytes ? o.mem_budget_bytes : (u64)ncap * 40 + (u64)ecap * 4;
+    c->budget = o.mem_budget_bytes ? o.mem_budget_bytes : (u64)ncap * 36 + (u64)ecap * 4;
     c->free_gids.reserve(kMaxGraphs);
     for (u32 g = kMaxGraphs; g-- > 0;)
         c->free_gids.push_back(g);
@@ -419,6 +451,12 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
         cudaHostAlloc((void **)&c->h_status, kMaxGraphs * sizeof(i32), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void **)&c->d_status, c->h_status, 0) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_sub, (size_t)kSubRing * sizeof(SubEntry), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_comp, (size_t)kSubRing * 8, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->d_comp, c->h_comp, 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_stop, 64, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->d_stop, c->h_stop, 0) != cudaSuccess ||
         cudaEventCreate(&c->ev_k0) != cudaSuccess || cudaEventCreate(&c->ev_k1) != cudaSuccess) {
         tg_ctx_destroy(c);
         return TG_ERR_CUDA;
@@ -453,8 +491,19 @@ int tg_ctx_destroy(tg_ctx *c)
         cudaFreeHost(c->h_status);
     if (c->h_stage)
         cudaFreeHost(c->h_stage);
+    if (c->h_sub)
+        cudaFreeHost(c->h_sub);
+    if (c->h_comp)
+        cudaFreeHost(c->h_comp);
+    if (c->h_stop)
+        cudaFreeHost(c->h_stop);
+    delete[] c->by_gid;
     if (c->capture_stream)
         cudaStreamDestroy(c->capture_stream);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
     if (c->ev_k0)
         cudaEventDestroy(c->ev_k0);
     if (c->ev_k1)
@@ -530,23 +579,31 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
     if (n_src == 0)
         return TG_ERR_NO_SOURCE;
 
-    // ---- pool space
-    const u64 bytes = (u64)n * 40 + ((u64)m + n_src) * 4;
+    // ---- pool space: a chunk-aligned execution range, and in the edge pool
+    // the successor lists, the sources and the pristine record image
+    const u64 n_chunks = ((u64)n + kChunk - 1) >> kChunkShift;
+    const u64 bytes = n_chunks * kChunk * 36 + ((u64)m + n_src + 64 + 8ull * n) * 4;
     if (c->used + bytes > c->budget || c->free_gids.empty())
         return TG_ERR_BUDGET;
     tg_graph *g = new (std::nothrow) tg_graph();
     if (!g)
         return TG_ERR_INVALID;
-    if (!c->nodes.alloc(n, g->node_off)) {
+    if (!c->nodes.alloc(n_chunks, g->chunk_off)) {
         delete g;
         return TG_ERR_BUDGET;
     }
-    g->edge_len = (u64)m + n_src;
+    g->n_chunks = n_chunks;
+    g->node_off = g->chunk_off << kChunkShift;
+    // the pristine image starts on a 256-byte boundary (64 entries), so its
+    // device-to-device copies stay on the copy engines
+    const u64 lead = (u64)m + n_src;
+    g->edge_len = lead + 64 + 8ull * n;
     if (!c->edge_pool.alloc(g->edge_len, g->edge_off)) {
-        c->nodes.release(g->node_off, n);
+        c->nodes.release(g->chunk_off, n_chunks);
         delete g;
         return TG_ERR_BUDGET;
     }
+    g->pristine_off = (g->edge_off + lead + 63) & ~(u64)63;
     g->gid = c->free_gids.back();
     c->free_gids.pop_back();
     c->used += bytes;
@@ -558,24 +615,23 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
     g->seed = seed;
     g->bytes = bytes;
 
-    // ---- pack: 32-byte node records, successors in insertion order, sources
-    const size_t slot_bytes = (size_t)n * sizeof(NodeSlot);
-    const size_t gid_bytes = (size_t)n * 4;
+    // ---- pack: successors in insertion order (graph-local ids), sources,
+    // then the 32-byte task records (W = strong in-degree, cnt = dig = 0)
     const size_t edge_bytes = (size_t)g->edge_len * 4;
-    int rc = ensure_stage(c, slot_bytes + gid_bytes + edge_bytes + 256);
+    const size_t chunk_bytes = (size_t)n_chunks * 4;
+    int rc = ensure_stage(c, edge_bytes + chunk_bytes + 512);
     if (rc != TG_OK) {
         tg_graph_destroy(c, g);
         return rc;
     }
     cudaStreamSynchronize(c->stream);   // staging buffer may still feed an earlier copy
-    NodeSlot *hs = (NodeSlot *)c->h_stage;
-    u32 *hg = (u32 *)(c->h_stage + slot_bytes);
-    u32 *he = (u32 *)(c->h_stage + slot_bytes + gid_bytes);
-    const u32 node_base = (u32)g->node_off;
+    u32 *he = (u32 *)c->h_stage;
+    NodeSlot *hs = (NodeSlot *)(he + (g->pristine_off - g->edge_off));
+    u32 *hc = (u32 *)(c->h_stage + edge_bytes);
     const u32 edge_base = (u32)g->edge_off;
     u32 acc = 0;
     for (u32 v = 0; v < n; ++v) {
-        NodeSlot &s = hs[v];
+        NodeSlot s;
         const u32 kind = kinds[v];
         u32 arg = 0;
         if (kind == TG_COND_LOOP)
@@ -589,33 +645,35 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
         s.W = sin[v];
         s.cnt = 0;
         s.dig = 0;
-        hg[v] = g->gid;
+        memcpy(&hs[v], &s, sizeof(s));
         outdeg[v] = acc;   // reuse as the fill cursor
         acc += (u32)(s.deg & 0xFFFFu);
     }
     for (u32 e = 0; e < m; ++e)
-        he[outdeg[src[e]]++] = node_base + dst[e];
+        he[outdeg[src[e]]++] = dst[e];
     for (u32 v = 0, k = 0; v < n; ++v)
         if (sin[v] == 0 && win[v] == 0)
-            he[m + k++] = node_base + v;
+            he[m + k++] = v;
+    for (u64 k = 0; k < n_chunks; ++k)
+        hc[k] = g->gid;
     const u64 t1 = now_ns();
 
     GDesc d{};
     d.pe = 0;
     d.status = 0;
     d.seed = seed;
-    d.node_off = node_base;
+    d.node_off = (u32)g->node_off;
     d.n = n;
     d.src_off = edge_base + m;
     d.n_src = n_src;
     d.exec_cap = (u32)std::min<u64>(c->opts.exec_cap, 0xFFFFFFFFull);
-    static_assert(sizeof(GDesc) <= 256, "stage tail");
-    memcpy(c->h_stage + slot_bytes + gid_bytes + edge_bytes, &d, sizeof(d));
-    cudaError_t e1 = cudaMemcpyAsync(c->slots + g->node_off, hs, slot_bytes, cudaMemcpyHostToDevice, c->stream);
-    cudaError_t e2 = cudaMemcpyAsync(c->gidv + g->node_off, hg, gid_bytes, cudaMemcpyHostToDevice, c->stream);
-    cudaError_t e3 = cudaMemcpyAsync(c->edges + g->edge_off, he, edge_bytes, cudaMemcpyHostToDevice, c->stream);
-    cudaError_t e4 = cudaMemcpyAsync(c->descs + g->gid, c->h_stage + slot_bytes + gid_bytes + edge_bytes,
-                                     sizeof(GDesc), cudaMemcpyHostToDevice, c->stream);
+    memcpy(c->h_stage + edge_bytes + chunk_bytes, &d, sizeof(d));
+    cudaError_t e1 = cudaMemcpyAsync(c->edges + g->edge_off, he, edge_bytes, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e2 = cudaMemcpyAsync(c->slots + g->node_off, c->edges + g->pristine_off, (size_t)n * sizeof(NodeSlot),
+                                     cudaMemcpyDeviceToDevice, c->stream);
+    cudaError_t e3 = cudaMemcpyAsync(c->chunk_gid + g->chunk_off, hc, chunk_bytes, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e4 = cudaMemcpyAsync(c->descs + g->gid, c->h_stage + edge_bytes + chunk_bytes, sizeof(GDesc),
+                                     cudaMemcpyHostToDevice, c->stream);
     cudaError_t e5 = cudaStreamSynchronize(c->stream);
     if (e1 || e2 || e3 || e4 || e5) {
         tg_graph_destroy(c, g);
@@ -627,14 +685,100 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
     return TG_OK;
 }
 
+}  // extern "C"
+
+// Write an instance's records (from the pristine image), chunk table and
+// descriptor on the side stream; later launches wait for `ready`.
+static int instance_setup(tg_ctx *c, tg_graph *g)
+{
+    tg_graph *src = g->tmpl ? g->tmpl : g;
+    std::vector<u32> hc(g->n_chunks, g->gid);
+    GDesc d{};
+    d.seed = g->seed;
+    d.node_off = (u32)g->node_off;
+    d.n = g->n;
+    d.src_off = (u32)(src->edge_off + src->m);
+    d.n_src = g->n_src;
+    d.exec_cap = (u32)std::min<u64>(c->opts.exec_cap, 0xFFFFFFFFull);
+    TG_CUDA(cudaMemcpyAsync(c->slots + g->node_off, c->edges + src->pristine_off, (size_t)g->n * sizeof(NodeSlot),
+                            cudaMemcpyDeviceToDevice, c->side));
+    TG_CUDA(cudaMemcpyAsync(c->chunk_gid + g->chunk_off, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice, c->side));
+    TG_CUDA(cudaMemcpyAsync(c->descs + g->gid, &d, sizeof(d), cudaMemcpyHostToDevice, c->side));
+    if (!g->ready)
+        TG_CUDA(cudaEventCreateWithFlags(&g->ready, cudaEventDisableTiming));
+    TG_CUDA(cudaEventRecord(g->ready, c->side));
+    g->setup_pending = false;
+    return TG_OK;
+}
+
+extern "C" {
+
+int tg_instance_create(tg_ctx *c, tg_graph *t, tg_graph **out)
+{
+    if (!c || !t || !out || t->ctx != c)
+        return TG_ERR_INVALID;
+    *out = nullptr;
+    tg_graph *src = t->tmpl ? t->tmpl : t;
+    const u64 bytes = src->n_chunks * kChunk * 36;
+    if (c->used + bytes > c->budget || c->free_gids.empty())
+        return TG_ERR_BUDGET;
+    u64 chunk_off = 0;
+    if (!c->nodes.alloc(src->n_chunks, chunk_off))
+        return TG_ERR_BUDGET;
+    tg_graph *g = new (std::nothrow) tg_graph();
+    if (!g) {
+        c->nodes.release(chunk_off, src->n_chunks);
+        return TG_ERR_INVALID;
+    }
+    *g = *src;
+    g->chunk_off = chunk_off;
+    g->tmpl = src;
+    g->n_inst = 0;
+    g->busy = nullptr;
+    g->ready = nullptr;
+    g->node_off = g->chunk_off << kChunkShift;
+    g->edge_len = 0;   // the packed form stays with the template
+    g->bytes = bytes;
+    g->pack_ns = 0;
+    g->gid = c->free_gids.back();
+    c->free_gids.pop_back();
+    c->used += bytes;
+    src->n_inst++;
+    if (c->serving) {
+        // the resident scheduler writes the descriptor and chunk table when
+        // it claims the instance's first submission
+        g->setup_pending = true;
+        *out = g;
+        return TG_OK;
+    }
+    const u64 t0 = now_ns();
+    int rc = instance_setup(c, g);
+    if (rc != TG_OK) {
+        tg_graph_destroy(c, g);
+        return rc;
+    }
+    g->upload_ns = now_ns() - t0;
+    *out = g;
+    return TG_OK;
+}
+
 int tg_graph_destroy(tg_ctx *c, tg_graph *g)
 {
     if (!c || !g || g->ctx != c)
         return TG_ERR_INVALID;
+    if (g->n_inst > 0 || g->serve_ticket != 0)
+        return TG_ERR_BUSY;   // instances still use its packed form, or it is being served
     if (g->busy)
         cudaEventSynchronize(g->busy);
-    c->nodes.release(g->node_off, g->n);
-    c->edge_pool.release(g->edge_off, g->edge_len);
+    if (g->ready) {
+        cudaEventSynchronize(g->ready);
+        cudaEventDestroy(g->ready);
+    }
+    c->nodes.release(g->chunk_off, g->n_chunks);
+    if (g->edge_len)
+        c->edge_pool.release(g->edge_off, g->edge_len);
+    if (g->tmpl)
+        g->tmpl->n_inst--;
     c->free_gids.push_back(g->gid);
     c->used -= g->bytes;
     for (auto it = c->subs.begin(); it != c->subs.end();) {
@@ -664,15 +808,26 @@ int tg_graph_get_info(const tg_graph *g, tg_graph_info *info)
     return TG_OK;
 }
 
+static int serve_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket);
+
 int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
 {
     if (!c || !g || g->ctx != c || !ticket)
         return TG_ERR_INVALID;
+    if (c->serving)
+        return serve_submit(c, g, ticket);
     if (graph_busy(g))
         return TG_ERR_BUSY;
     int rc = clear_if_dirty(c);
     if (rc != TG_OK)
         return rc;
+    if (g->setup_pending) {
+        int rc2 = instance_setup(c, g);
+        if (rc2 != TG_OK)
+            return rc2;
+    }
+    if (g->ready)
+        TG_CUDA(cudaStreamWaitEvent(c->stream, g->ready, 0));
     KParams p = base_params(c, c->geo);
     p.lt = nullptr;
     p.n_graphs = 1;
@@ -707,10 +862,14 @@ static int finish_sub(tg_ctx *c, Submission &s)
     return s.status;
 }
 
+static int serve_poll(tg_ctx *c, uint64_t ticket);
+
 int tg_poll(tg_ctx *c, uint64_t ticket)
 {
     if (!c)
         return TG_ERR_INVALID;
+    if (c->serving || c->serve_done.count(ticket))
+        return serve_poll(c, ticket);
     auto it = c->subs.find(ticket);
     if (it == c->subs.end())
         return TG_ERR_INVALID;
@@ -729,6 +888,15 @@ int tg_wait(tg_ctx *c, uint64_t ticket)
 {
     if (!c)
         return TG_ERR_INVALID;
+    if (c->serving || c->serve_done.count(ticket)) {
+        for (;;) {
+            int st = serve_poll(c, ticket);
+            if (st != TG_PENDING)
+                return st;
+            if (cudaStreamQuery(c->stream) != cudaErrorNotReady)
+                return serve_poll(c, ticket);   // the server ended
+        }
+    }
     auto it = c->subs.find(ticket);
     if (it == c->subs.end())
         return TG_ERR_INVALID;
@@ -742,6 +910,8 @@ int tg_wait(tg_ctx *c, uint64_t ticket)
 
 int tg_run(tg_ctx *c, tg_graph *g)
 {
+    if (c && c->serving)
+        return TG_ERR_BUSY;
     uint64_t t = 0;
     int rc = tg_submit(c, g, &t);
     if (rc != TG_OK)
@@ -768,13 +938,16 @@ int tg_result_copy(tg_ctx *c, const tg_graph *g, uint32_t *out, uint32_t *cnt, u
 {
     if (!c || !g || g->ctx != c)
         return TG_ERR_INVALID;
-    TG_CUDA(cudaStreamSynchronize(c->stream));
+    if (!c->serving)
+        TG_CUDA(cudaStreamSynchronize(c->stream));
     if (out)
-        TG_CUDA(cudaMemcpy(out, c->outv + g->node_off, (size_t)g->n * 4, cudaMemcpyDeviceToHost));
-    if (cnt || dig || total_execs) {
+        TG_CUDA(cudaMemcpyAsync(out, c->outv + g->node_off, (size_t)g->n * 4, cudaMemcpyDeviceToHost, c->side));
+    TG_CUDA(cudaStreamSynchronize(c->side));
+    if (out || cnt || dig || total_execs) {
         std::vector<NodeSlot> tmp(g->n);
-        TG_CUDA(cudaMemcpy(tmp.data(), c->slots + g->node_off, (size_t)g->n * sizeof(NodeSlot),
-                           cudaMemcpyDeviceToHost));
+        TG_CUDA(cudaMemcpyAsync(tmp.data(), c->slots + g->node_off, (size_t)g->n * sizeof(NodeSlot),
+                                cudaMemcpyDeviceToHost, c->side));
+        TG_CUDA(cudaStreamSynchronize(c->side));
         u64 tot = 0;
         for (u32 v = 0; v < g->n; ++v) {
             const u32 k = tmp[v].cnt & ~kInflight;
@@ -782,6 +955,8 @@ int tg_result_copy(tg_ctx *c, const tg_graph *g, uint32_t *out, uint32_t *cnt, u
                 cnt[v] = k;
             if (dig)
                 dig[v] = tmp[v].dig;
+            if (out && k == 0)
+                out[v] = 0;   // never executed (an instance's range is not zeroed)
             tot += k;
         }
         if (total_execs)
@@ -883,12 +1058,23 @@ int tg_batch_launch(tg_ctx *c, tg_batch *b)
 {
     if (!c || !b || b->ctx != c)
         return TG_ERR_INVALID;
+    if (c->serving)
+        return TG_ERR_BUSY;
     for (tg_graph *g : b->gs)
         if (graph_busy(g))
             return TG_ERR_BUSY;
     int rc = clear_if_dirty(c);
     if (rc != TG_OK)
         return rc;
+    for (tg_graph *g : b->gs) {
+        if (g->setup_pending) {
+            int rc2 = instance_setup(c, g);
+            if (rc2 != TG_OK)
+                return rc2;
+        }
+        if (g->ready)
+            TG_CUDA(cudaStreamWaitEvent(c->stream, g->ready, 0));
+    }
     TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
     TG_CUDA(cudaGraphLaunch(b->exec, c->stream));
     TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
@@ -1195,3 +1381,251 @@ int tg_bench_atomics(tg_ctx *c, uint64_t count, uint64_t footprint_words, uint64
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// server mode: a resident scheduler fed through a submission ring
+// ---------------------------------------------------------------------------
+static void drain_completions(tg_ctx *c)
+{
+    for (;;) {
+        const u64 rec = ((volatile u64 *)c->h_comp)[c->comp_read & (kSubRing - 1u)];
+        if ((rec >> 32) != (u32)(c->comp_read + 1u))
+            break;
+        const u32 gid = (u32)(rec & 0xFFFFu);
+        const int st = (int)(int16_t)(uint16_t)((rec >> 16) & 0xFFFFu);
+        tg_graph *g = c->by_gid[gid];
+        if (g) {
+            c->serve_done[g->serve_ticket] = st;
+            c->newly_done.push_back(g->serve_ticket);
+            g->serve_ticket = 0;
+            c->by_gid[gid] = nullptr;
+        }
+        c->comp_read++;
+    }
+}
+
+static int serve_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
+{
+    if (g->serve_ticket != 0 || graph_busy(g))
+        return TG_ERR_BUSY;
+    tg_graph *src = g->tmpl ? g->tmpl : g;
+    // re-arm on the side stream: fresh task records from the pristine image
+    // (join words, counts, digests), then the ring entry -- stream order makes
+    // the records visible before the scheduler can see the entry
+    const u64 seq = c->sub_seq++;
+    SubEntry &h = c->h_sub[seq & (kSubRing - 1u)];
+    h.seq = (u32)(seq + 1u);
+    h.gid = g->gid;
+    h.node_off = (u32)g->node_off;
+    h.n = g->n;
+    h.seed = g->seed;
+    h.src_off = (u32)(src->edge_off + src->m);
+    h.n_src = g->n_src;
+    h.exec_cap = (u32)std::min<u64>(c->opts.exec_cap, 0xFFFFFFFFull);
+    g->setup_pending = false;   // the scheduler writes descriptor and chunk table on claim
+    TG_CUDA(cudaMemcpyAsync(c->slots + g->node_off, c->edges + src->pristine_off, (size_t)g->n * sizeof(NodeSlot),
+                            cudaMemcpyDeviceToDevice, c->side));
+    // the entry's fields first, its sequence word last: a scheduler that sees
+    // the new seq then reads complete fields (stream order of the copies)
+    SubEntry *dst = &c->sub[seq & (kSubRing - 1u)];
+    TG_CUDA(cudaMemcpyAsync(&dst->gid, &h.gid, sizeof(SubEntry) - sizeof(u32), cudaMemcpyHostToDevice, c->side));
+    TG_CUDA(cudaMemcpyAsync(&dst->seq, &h.seq, sizeof(u32), cudaMemcpyHostToDevice, c->side));
+    g->serve_ticket = c->next_ticket++;
+    c->by_gid[g->gid] = g;
+    *ticket = g->serve_ticket;
+    return TG_OK;
+}
+
+static int serve_poll(tg_ctx *c, uint64_t ticket)
+{
+    drain_completions(c);
+    auto it = c->serve_done.find(ticket);
+    if (it != c->serve_done.end())
+        return it->second;
+    if (!c->serving)
+        return TG_ERR_INVALID;
+    return TG_PENDING;
+}
+
+extern "C" {
+
+int tg_serve_start(tg_ctx *c, uint64_t time_limit_ns)
+{
+    if (!c)
+        return TG_ERR_INVALID;
+    if (c->serving)
+        return TG_ERR_BUSY;
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    if (!c->by_gid) {
+        c->by_gid = new (std::nothrow) tg_graph *[kMaxGraphs];
+        if (!c->by_gid)
+            return TG_ERR_INVALID;
+    }
+    for (u32 i = 0; i < kMaxGraphs; ++i)
+        c->by_gid[i] = nullptr;
+    int rc = clear_if_dirty(c);
+    if (rc != TG_OK)
+        return rc;
+    Geometry g = c->geo;
+    int per_sm = 0;
+    if (sched_occupancy(g.threads, sched_dyn_smem(g.ring, (u32)(g.threads / 32)), &per_sm, true) != cudaSuccess ||
+        per_sm <= 0)
+        return TG_ERR_CUDA;
+    // one block per SM: the resident server leaves room on every SM for the
+    // copy kernels that re-arm instances (device-to-device record copies)
+    g.blocks = std::min(g.blocks, std::min(c->sm_count, kMaxBlocks));
+    c->serve_geo = g;
+    *(volatile u32 *)c->h_stop = 0u;
+    memset(c->h_comp, 0, (size_t)kSubRing * 8);
+    c->sub_seq = 0;
+    c->comp_read = 0;
+    TG_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(LaunchCtl), c->stream));
+    TG_CUDA(cudaMemsetAsync(c->sub, 0, (size_t)kSubRing * sizeof(SubEntry), c->stream));
+    TG_CUDA(cudaMemsetAsync(c->dqc, 0, (size_t)kMaxBlocks * sizeof(QCtr), c->stream));
+    TG_CUDA(cudaMemsetAsync(c->thief_slots, 0, (size_t)1024 * 128, c->stream));
+    TG_CUDA(cudaMemsetAsync(c->stats, 0, (size_t)kMaxBlocks * ST_COUNT * sizeof(u64), c->stream));
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    KParams p = base_params(c, g);
+    p.lt = nullptr;
+    p.n_graphs = 0;
+    p.single_gid = 0;
+    p.time_limit_ns = time_limit_ns ? time_limit_ns : 60ull * 1000 * 1000 * 1000;
+    TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    TG_CUDA(launch_sched(p, g.blocks, g.threads, c->stream, true));
+    TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    c->last_geo = g;
+    c->timed = true;
+    c->serving = true;
+    return TG_OK;
+}
+
+int tg_serve_stop(tg_ctx *c)
+{
+    if (!c)
+        return TG_ERR_INVALID;
+    if (!c->serving)
+        return TG_ERR_INVALID;
+    // the stop word lives in device memory (idle blocks poll it); write it
+    // behind every queued submission
+    *(volatile u32 *)c->h_stop = 1u;
+    cudaError_t e = cudaMemcpyAsync(&c->ctl->stop, c->h_stop, sizeof(u32), cudaMemcpyHostToDevice, c->side);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    drain_completions(c);
+    c->serving = false;
+    if (e != cudaSuccess)
+        return TG_ERR_CUDA;
+    LaunchCtl h{};
+    TG_CUDA(cudaMemcpy(&h, c->ctl, sizeof(h), cudaMemcpyDeviceToHost));
+    // graphs still in flight end with the abort code (or TIMEOUT)
+    const int code = h.abort_code != 0 ? h.abort_code : TG_OK;
+    for (u32 i = 0; i < kMaxGraphs; ++i) {
+        if (tg_graph *g = c->by_gid[i]) {
+            c->serve_done[g->serve_ticket] = code != TG_OK ? code : TG_ERR_CANCELLED;
+            g->serve_ticket = 0;
+            c->by_gid[i] = nullptr;
+        }
+    }
+    c->dirty = true;
+    return code;
+}
+
+}  // extern "C"
+
+extern "C" int tg_serve_replay(tg_ctx *c, tg_graph *const *templates, uint32_t n_templates, const uint32_t *which,
+                               const uint64_t *arrival_ns, uint32_t n_requests, uint64_t *latency_ns, int *status,
+                               uint32_t *max_in_flight, tg_graph **keep)
+{
+    if (!c || !c->serving || !templates || !which || !arrival_ns || !latency_ns || !status)
+        return TG_ERR_INVALID;
+    for (uint32_t i = 0; i < n_requests; ++i)
+        if (which[i] >= n_templates || !templates[which[i]] || templates[which[i]]->ctx != c)
+            return TG_ERR_INVALID;
+    struct Flight {
+        uint32_t req;
+        tg_graph *inst;
+    };
+    std::map<u64, Flight> flight;
+    std::vector<uint32_t> waiting;   // FIFO of admitted-to-host, not yet on the device
+    size_t wait_head = 0;
+    uint32_t next = 0, done = 0, peak = 0;
+    int first_err = TG_OK;
+    c->newly_done.clear();
+    const u64 t0 = now_ns();
+    while (done < n_requests) {
+        bool progress = false;
+        u64 now = now_ns() - t0;
+        while (next < n_requests && arrival_ns[next] <= now)
+            waiting.push_back(next++);
+        // admission: an instance per request while budget and slots allow
+        while (wait_head < waiting.size()) {
+            const uint32_t r = waiting[wait_head];
+            tg_graph *inst = nullptr;
+            int rc = tg_instance_create(c, templates[which[r]], &inst);
+            if (rc == TG_ERR_BUDGET && !flight.empty())
+                break;   // wait for a finished graph to free memory or a slot
+            wait_head++;
+            progress = true;
+            if (rc == TG_OK) {
+                uint64_t t = 0;
+                rc = serve_submit(c, inst, &t);
+                if (rc == TG_OK) {
+                    flight[t] = Flight{r, inst};
+                    peak = std::max<uint32_t>(peak, (uint32_t)flight.size());
+                    continue;
+                }
+                tg_graph_destroy(c, inst);
+            }
+            status[r] = rc;
+            latency_ns[r] = 0;
+            if (first_err == TG_OK)
+                first_err = rc;
+            done++;
+        }
+        // completions: free the instance at once
+        drain_completions(c);
+        if (!c->newly_done.empty()) {
+            now = now_ns() - t0;
+            for (u64 t : c->newly_done) {
+                auto it = flight.find(t);
+                if (it == flight.end())
+                    continue;
+                const uint32_t r = it->second.req;
+                const int st = c->serve_done[t];
+                c->serve_done.erase(t);
+                status[r] = st;
+                latency_ns[r] = now > arrival_ns[r] ? now - arrival_ns[r] : 0;
+                if (st != TG_OK && first_err == TG_OK)
+                    first_err = st;
+                if (keep)
+                    keep[r] = it->second.inst;
+                else
+                    tg_graph_destroy(c, it->second.inst);
+                flight.erase(it);
+                done++;
+            }
+            c->newly_done.clear();
+            progress = true;
+        }
+        if (!progress && cudaStreamQuery(c->stream) != cudaErrorNotReady) {
+            // the resident scheduler ended (time limit / fault): fail the rest
+            for (auto &kv : flight) {
+                status[kv.second.req] = TG_ERR_TIMEOUT;
+                if (keep)
+                    keep[kv.second.req] = kv.second.inst;
+                done++;
+            }
+            for (size_t i = wait_head; i < waiting.size(); ++i, ++done)
+                status[waiting[i]] = TG_ERR_TIMEOUT;
+            for (; next < n_requests; ++next, ++done)
+                status[next] = TG_ERR_TIMEOUT;
+            if (first_err == TG_OK)
+                first_err = TG_ERR_TIMEOUT;
+            break;
+        }
+    }
+    if (max_in_flight)
+        *max_in_flight = peak;
+    return first_err;
+}
+

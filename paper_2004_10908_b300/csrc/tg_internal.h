@@ -54,6 +54,19 @@ struct alignas(128) QCtr {
     u32 pad1[31];
 };
 
+// One submission of the server-mode ring: written by the host (copy engine),
+// claimed by a thief when seq == its ticket + 1.
+struct alignas(32) SubEntry {
+    u32 seq;
+    u32 gid;
+    u32 node_off;
+    u32 n;
+    u32 seed;
+    u32 src_off;
+    u32 n_src;
+    u32 exec_cap;
+};
+
 // Launch-wide control words (each on its own 128-byte line).
 struct alignas(128) LaunchCtl {
     u32 graphs_left;
@@ -65,6 +78,12 @@ struct alignas(128) LaunchCtl {
     QCtr inj;
     u32 avail[32];   // bit b: block b's public deque may hold work (blocks < 1024)
     u32 pad3[96];
+    u32 sub_head;    // server mode: next submission to claim
+    u32 pad4[31];
+    u32 comp_tail;   // server mode: completion records written
+    u32 pad5[31];
+    u32 stop;        // server mode: set by the host (copy engine) to end the server
+    u32 pad6[31];
 };
 
 enum StatIdx {
@@ -77,12 +96,14 @@ constexpr u64 kEmpty = 0xFFFFFFFFFFFFFFFFull;
 constexpr u32 kStrongBit = 0x80000000u;   // in a ready entry's low word
 constexpr u32 kInflight = 0x80000000u;    // in NodeSlot::cnt
 constexpr u32 kMaxNodeIndex = 0x7FFFFFFEu;
+constexpr u32 kChunkShift = 8;            // node ranges are allocated in 256-task chunks
+constexpr u32 kChunk = 1u << kChunkShift;
 
 struct KParams {
     NodeSlot *slots;
     u32 *outv;
-    const u32 *gidv;
-    const u32 *edges;
+    const u32 *chunk_gid;  // graph slot of every 256-task chunk of the node pool
+    const u32 *edges;      // successor lists and sources, as graph-local task ids
     GDesc *descs;
     const LEntry *lt;      // launch table (nullptr: single graph `single_gid`)
     u32 n_graphs;
@@ -110,14 +131,19 @@ struct KParams {
     u64 time_limit_ns;
     volatile u32 *cancel;  // host-mapped cancel flag (may be null)
     i32 *status_out;       // host-mapped per-gid statuses (may be null)
+    // server mode
+    const SubEntry *sub;   // submission ring (device memory), sub_mask + 1 entries
+    u32 sub_mask;
+    u32 comp_mask;
+    volatile u64 *comp;    // completion ring (host-mapped): seq << 32 | status << 16 | gid
 };
 
 // Launch helpers implemented in tg_kernels.cu (all enqueue on `st`).
 cudaError_t launch_rearm(const KParams &p, cudaStream_t st);
-cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t st, bool serve = false);
 cudaError_t launch_finalize(const KParams &p, cudaStream_t st);
 cudaError_t launch_clear(u64 *slots, size_t count, cudaStream_t st);
-cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm);
+cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bool serve = false);
 size_t sched_dyn_smem(u32 smem_entries, u32 warps);
 cudaError_t launch_bench_payload(u64 count, u32 rounds, u32 *checksum, cudaStream_t st);
 cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink, cudaStream_t st);

@@ -249,6 +249,7 @@ __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u6
 // Examine the result of the previous iteration's pending-count update: a
 // graph whose pending count reached zero is complete; one whose execution
 // count passed its cap is poisoned with TG_ERR_EXEC_LIMIT.
+template <bool kServe>
 __device__ __forceinline__ void settle_finish(const KParams &p, bool &pend, u64 old, u64 delta, u32 g, u32 cap)
 {
     if (!pend)
@@ -256,9 +257,30 @@ __device__ __forceinline__ void settle_finish(const KParams &p, bool &pend, u64 
     const u64 nw = old + delta;
     if ((u32)(nw >> 32) > cap)
         atomicCAS(&p.descs[g].status, 0, TG_ERR_EXEC_LIMIT);
-    if ((u32)nw == 0u)
-        atomicSub(&p.ctl->graphs_left, 1u);
+    if ((u32)nw == 0u) {
+        if (kServe) {
+            // the graph is done: post a completion record to the host
+            fence_acq_rel_gpu();
+            const i32 st = vldi(&p.descs[g].status);
+            const u32 idx = atomicAdd(&p.ctl->comp_tail, 1u);
+            p.comp[idx & p.comp_mask] = ((u64)(idx + 1u) << 32) | ((u64)((u32)st & 0xFFFFu) << 16) | (u64)(g & 0xFFFFu);
+            __threadfence_system();
+        } else {
+            atomicSub(&p.ctl->graphs_left, 1u);
+        }
+    }
     pend = false;
+}
+
+// Loads of data that is immutable while its graph exists: through L1 for a
+// one-shot launch; through L2 for the resident server, whose node ranges and
+// graph slots are recycled while it runs.
+template <bool kServe, typename T>
+__device__ __forceinline__ T ld_imm(const T *ptr)
+{
+    if (kServe)
+        return __ldcg(ptr);
+    return __ldg(ptr);
 }
 
 // Stage the new activations of the lanes with `has` in the warp's buffer;
@@ -292,6 +314,7 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
     }
 }
 
+template <bool kServe>
 __global__ void sched_kernel(KParams p)
 {
     extern __shared__ u64 s_ring[];
@@ -317,8 +340,8 @@ __global__ void sched_kernel(KParams p)
     __syncthreads();
 
     const bool race_check = (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
-    const bool single = p.lt == nullptr;   // one graph: every activation has gid == single_gid
-    const u32 single_cap = single ? __ldg(&p.descs[p.single_gid].exec_cap) : 0u;
+    const bool single = !kServe && p.lt == nullptr;   // one graph: every activation has gid == single_gid
+    const u32 single_cap = single ? ld_imm<kServe>(&p.descs[p.single_gid].exec_cap) : 0u;
     const u64 t0 = globaltimer();
     const u64 deadline = t0 + p.time_limit_ns;
 
@@ -352,7 +375,7 @@ __global__ void sched_kernel(KParams p)
     int nh = 0;
     // per-lane cache of the lane's graph descriptor; the status word is
     // re-read every 16 activations, so a poisoned graph drains soon after
-    u32 c_gid = kEmpty32, c_seed = 0, c_cap = 0, c_age = 0;
+    u32 c_gid = kEmpty32, c_seed = 0, c_cap = 0, c_age = 0, c_base = 0;
     i32 c_status = 0;
 
     for (;;) {
@@ -368,7 +391,7 @@ __global__ void sched_kernel(KParams p)
             if (k) {
                 st_local++;
             } else {
-                settle_finish(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+                settle_finish<kServe>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
                 // ---- idle.  One warp per block at a time is the block's thief
                 // (Alg. 6/7), and at most max_thieves blocks steal at once; only
                 // thieves poll launch-wide state, the other idle warps wait on
@@ -391,7 +414,8 @@ __global__ void sched_kernel(KParams p)
                         // low rate (one read per block every few microseconds)
                         int stop = 0;
                         if (lane == 0 && ((++noslot & 3u) == 0u)) {
-                            if (vld32(&p.ctl->graphs_left) == 0u || vldi(&p.ctl->abort_code) != 0) {
+                            const bool done = kServe ? (vld32(&p.ctl->stop) != 0u) : (vld32(&p.ctl->graphs_left) == 0u);
+                            if (done || vldi(&p.ctl->abort_code) != 0) {
                                 stop = 1;
                             } else if (globaltimer() > deadline) {
                                 atomicCAS(&p.ctl->abort_code, 0, TG_ERR_TIMEOUT);
@@ -408,7 +432,64 @@ __global__ void sched_kernel(KParams p)
                         backoff = min(backoff * 2u, 4096u);
                     continue;
                 }
-                k = ring_pop(w.own, false, lane, e, w.err);
+                if (kServe) {
+                    // claim the next submitted graph, re-arm its pending
+                    // count and status, and take its sources (Algorithm 8)
+                    u32 cg = kEmpty32;
+                    SubEntry subv{};
+                    if (lane == 0) {
+                        const u32 h = vld32(&p.ctl->sub_head);
+                        const SubEntry *se = &p.sub[h & p.sub_mask];
+                        if (vld32(&se->seq) == h + 1u && atomicCAS(&p.ctl->sub_head, h, h + 1u) == h) {
+                            cg = vld32(&se->gid);
+                            subv.node_off = vld32(&se->node_off);
+                            subv.n = vld32(&se->n);
+                            subv.seed = vld32(&se->seed);
+                            subv.src_off = vld32(&se->src_off);
+                            subv.n_src = vld32(&se->n_src);
+                            subv.exec_cap = vld32(&se->exec_cap);
+                        }
+                    }
+                    cg = __shfl_sync(kFull, cg, 0);
+                    subv.node_off = __shfl_sync(kFull, subv.node_off, 0);
+                    subv.n = __shfl_sync(kFull, subv.n, 0);
+                    subv.seed = __shfl_sync(kFull, subv.seed, 0);
+                    subv.src_off = __shfl_sync(kFull, subv.src_off, 0);
+                    subv.n_src = __shfl_sync(kFull, subv.n_src, 0);
+                    subv.exec_cap = __shfl_sync(kFull, subv.exec_cap, 0);
+                    if (cg != kEmpty32) {
+                        // the entry carries the graph's descriptor: write it and
+                        // the graph's chunk-table entries, then its sources
+                        GDesc &D = p.descs[cg];
+                        const u32 base = subv.node_off;
+                        const u32 n_src = subv.n_src;
+                        const u32 src_off = subv.src_off;
+                        if (lane == 0) {
+                            vst32(&D.seed, subv.seed);
+                            vst32(&D.node_off, base);
+                            vst32(&D.n, subv.n);
+                            vst32(&D.src_off, src_off);
+                            vst32(&D.n_src, n_src);
+                            vst32(&D.exec_cap, subv.exec_cap);
+                            vst64(&D.pe, (u64)n_src);
+                            vst32((u32 *)&D.status, 0u);
+                        }
+                        const u32 n_chunks = (subv.n + kChunk - 1u) >> kChunkShift;
+                        for (u32 i = (u32)lane; i < n_chunks; i += 32u)
+                            vst32(const_cast<u32 *>(&p.chunk_gid[(base >> kChunkShift) + i]), cg);
+                        fence_acq_rel_gpu();
+                        __syncwarp();
+                        for (u32 i = 0; i < n_src; i += 32u) {
+                            const bool h = i + (u32)lane < n_src;
+                            const u64 ent = h ? (u64)(base + __ldcg(&p.edges[src_off + i + (u32)lane])) : 0ull;
+                            emit(w, h, ent, lane, st_spill);
+                        }
+                        st_inj++;
+                        k = ring_pop(w.local, false, lane, e, w.err);
+                    }
+                }
+                if (k == 0)
+                    k = ring_pop(w.own, false, lane, e, w.err);
                 if (k) {
                     st_own++;
                 } else {
@@ -471,7 +552,8 @@ __global__ void sched_kernel(KParams p)
                     st_idle++;
                     int stop = 0;
                     if (lane == 0) {
-                        if (vld32(&p.ctl->graphs_left) == 0u || vldi(&p.ctl->abort_code) != 0) {
+                        const bool done = kServe ? (vld32(&p.ctl->stop) != 0u) : (vld32(&p.ctl->graphs_left) == 0u);
+                        if (done || vldi(&p.ctl->abort_code) != 0) {
                             stop = 1;
                         } else if (globaltimer() > deadline) {
                             atomicCAS(&p.ctl->abort_code, 0, TG_ERR_TIMEOUT);
@@ -523,14 +605,17 @@ __global__ void sched_kernel(KParams p)
         uint2 stt = make_uint2(0, 0);
         u32 gid = 0;
         if (act) {
-            imm = __ldg(reinterpret_cast<const uint4 *>(&p.slots[u]));
+            imm = ld_imm<kServe>(reinterpret_cast<const uint4 *>(&p.slots[u]));
             stt = __ldcg(reinterpret_cast<const uint2 *>(&p.slots[u].cnt));
-            gid = single ? p.single_gid : __ldg(&p.gidv[u]);
+            gid = single ? p.single_gid : ld_imm<kServe>(&p.chunk_gid[u >> kChunkShift]);
         }
         if (act) {
-            if (gid != c_gid || c_age >= 16u) {
-                c_seed = __ldg(&p.descs[gid].seed);
-                c_cap = __ldg(&p.descs[gid].exec_cap);
+            // the resident server recycles graph slots, so it re-reads the
+            // descriptor of every activation
+            if (kServe || gid != c_gid || c_age >= 16u) {
+                c_seed = ld_imm<kServe>(&p.descs[gid].seed);
+                c_cap = ld_imm<kServe>(&p.descs[gid].exec_cap);
+                c_base = ld_imm<kServe>(&p.descs[gid].node_off);
                 c_status = vldi(&p.descs[gid].status);
                 c_gid = gid;
                 c_age = 0;
@@ -563,7 +648,7 @@ __global__ void sched_kernel(KParams p)
             for (int j = 0; j < kRelUnroll; ++j) {
                 v_[j] = j0 + (u32)j < c;
                 ow_[j] = (u32)lane;
-                s_[j] = v_[j] ? __ldg(&p.edges[succ_off + j0 + (u32)j]) : 0u;
+                s_[j] = v_[j] ? c_base + ld_imm<kServe>(&p.edges[succ_off + j0 + (u32)j]) : 0u;
             }
         };
         auto fetch_flat = [&](u32 base) {
@@ -581,8 +666,9 @@ __global__ void sched_kernel(KParams p)
                 }
                 const u32 off_o = __shfl_sync(kFull, succ_off, o);
                 const u32 ex_o = __shfl_sync(kFull, excl, o);
+                const u32 base_o = __shfl_sync(kFull, c_base, o);
                 ow_[j] = (u32)o;
-                s_[j] = v_[j] ? __ldg(&p.edges[off_o + (eq - ex_o)]) : 0u;
+                s_[j] = v_[j] ? base_o + ld_imm<kServe>(&p.edges[off_o + (eq - ex_o)]) : 0u;
             }
         };
         if (per_lane) {
@@ -602,7 +688,7 @@ __global__ void sched_kernel(KParams p)
         }
 
         // the previous iteration's pending-count update arrives meanwhile
-        settle_finish(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+        settle_finish<kServe>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
 
         // a strong activation consumed its join word: re-arm it for the next
         // round (composes with releases of that round that arrive early)
@@ -665,7 +751,7 @@ __global__ void sched_kernel(KParams p)
         if (run && kind != TG_STATIC) {
             int r = cond_index(kind, arg, c_seed, lid, iter, succ_cnt);
             if (r >= 0 && (u32)r < succ_cnt) {
-                c_t = __ldg(&p.edges[succ_off + (u32)r]);
+                c_t = c_base + ld_imm<kServe>(&p.edges[succ_off + (u32)r]);
                 c_has = true;
                 mp++;
                 if (race_check) {
@@ -848,7 +934,7 @@ __global__ void sched_kernel(KParams p)
         }
     }
 
-    settle_finish(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+    settle_finish<kServe>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
     if (lane == 0) {
         atomicAdd(&s_stats[ST_POP_LOCAL], st_local);
         atomicAdd(&s_stats[ST_POP_OWN], st_own);
@@ -889,7 +975,7 @@ __global__ void rearm_kernel(KParams p)
     }
     if (blockIdx.x == 0) {
         for (u32 s = threadIdx.x; s < D.n_src; s += blockDim.x)
-            p.inj[(inj_base + s) & p.inj_mask] = (u64)p.edges[D.src_off + s];
+            p.inj[(inj_base + s) & p.inj_mask] = (u64)(D.node_off + p.edges[D.src_off + s]);
         if (threadIdx.x == 0) {
             D.pe = (u64)D.n_src;
             D.status = 0;
@@ -986,12 +1072,17 @@ size_t sched_dyn_smem(u32 smem_entries, u32 warps)
     return ((size_t)smem_entries + (size_t)warps * kStage) * sizeof(u64);
 }
 
-cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm)
+cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bool serve)
 {
-    cudaError_t e = cudaFuncSetAttribute(sched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    cudaError_t e = cudaFuncSetAttribute(sched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel, threads, dyn_smem);
+    e = cudaFuncSetAttribute(sched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    if (e != cudaSuccess)
+        return e;
+    if (serve)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<true>, threads, dyn_smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false>, threads, dyn_smem);
 }
 
 cudaError_t launch_rearm(const KParams &p, cudaStream_t st)
@@ -1003,9 +1094,13 @@ cudaError_t launch_rearm(const KParams &p, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t st)
+cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t st, bool serve)
 {
-    sched_kernel<<<blocks, threads, sched_dyn_smem(p.smem_mask + 1u, (u32)threads / 32u), st>>>(p);
+    const size_t smem = sched_dyn_smem(p.smem_mask + 1u, (u32)threads / 32u);
+    if (serve)
+        sched_kernel<true><<<blocks, threads, smem, st>>>(p);
+    else
+        sched_kernel<false><<<blocks, threads, smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -125,7 +125,7 @@ __global__ void na_pack_kernel(u32 n, u32 m, const u8 *kinds, const u32 *params,
         s.cnt = 0;
         s.dig = 0;
         slots[v] = s;
-        gidv[v] = 0;
+        gidv[v >> kChunkShift] = 0;
         for (u32 e = a; e < b; ++e)
             edges[e] = succ[e];
         if (strong[v] == 0 && weak[v] == 0) {
@@ -244,7 +244,7 @@ extern "C" int tg_run_noalloc(uint32_t n_nodes, const uint8_t *kinds, const uint
     KParams p{};
     p.slots = (NodeSlot *)(base + kOffSlots);
     p.outv = (u32 *)(base + kOffOut);
-    p.gidv = (const u32 *)(base + kOffGid);
+    p.chunk_gid = (const u32 *)(base + kOffGid);
     p.edges = (const u32 *)(base + kOffEdges);
     p.descs = (GDesc *)(base + kOffDesc);
     p.lt = nullptr;

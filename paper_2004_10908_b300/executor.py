@@ -79,6 +79,31 @@ class Executor:
         """Upload a workloads.Graph-like object (kinds, params, src, dst, seed)."""
         return self.create(g.kinds, g.params, g.src, g.dst, g.seed, weak, getattr(g, "name", ""))
 
+    def instance(self, gh: GraphHandle) -> GraphHandle:
+        """Another execution instance of gh (own state, shared packed form)."""
+        st, h = B.tg_instance_create(self.ctx, gh.handle)
+        if st != B.TG_OK:
+            raise B.TgError(st, "tg_instance_create")
+        return GraphHandle(self, h, gh.n, gh.m, gh.name)
+
+    # -- serving ------------------------------------------------------------
+    def serve_start(self, time_limit_ns=0):
+        st = B.tg_serve_start(self.ctx, time_limit_ns)
+        if st != B.TG_OK:
+            raise B.TgError(st, "tg_serve_start")
+
+    def serve_stop(self) -> int:
+        return B.tg_serve_stop(self.ctx)
+
+    def serve_replay(self, templates, which, arrival_ns, keep=False):
+        """Run a request trace through the server; see tg_serve_replay."""
+        st, lat, sts, peak, kept = B.tg_serve_replay(self.ctx, [t.handle for t in templates], which,
+                                                     arrival_ns, keep)
+        if kept is not None:
+            kept = [GraphHandle(self, h, templates[wi].n, templates[wi].m, templates[wi].name) if h else None
+                    for h, wi in zip(kept, which)]
+        return st, lat, sts, peak, kept
+
     def run(self, gh: GraphHandle) -> int:
         return B.tg_run(self.ctx, gh.handle)
 

@@ -136,7 +136,7 @@ def test_full_size_batch_sampled():
     """4,096 graphs, 33M tasks, one launch; 64 sampled graphs vs the oracle."""
     from paper_2004_10908_b300 import Executor
     gs = w.config4()
-    with Executor(arena_bytes=6 << 30, max_nodes=40_000_000, max_edges=200_000_000) as ex2:
+    with Executor(arena_bytes=8 << 30, max_nodes=40_000_000, max_edges=450_000_000) as ex2:
         hs = [ex2.graph(g) for g in gs]
         b = ex2.batch(hs)
         b.launch()
