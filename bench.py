@@ -1,19 +1,27 @@
 """Benchmark: device-resident task-graph execution on one B300.
 
-One step = one pass of the whole hot path over the workload: for each graph,
-re-arm its state (join words, counts, digests, queues, sources), run the
-persistent scheduler until every task has run, finalise the status.
-
-Default workload ("large static DAGs, plain form"): the 1,000 x 1,000
+Headline (`value`): the large static DAGs in plain form -- the 1,000 x 1,000
 layered random DAG (in-degree U{1..8}, 16 rounds) and the 1024 x 1024
-wavefront (256 rounds); 2,048,576 task executions per step.  Graph inputs
-are resident in HBM when the timed region starts; L2 (126 MB) is flushed
-between timed steps by writing a 512 MB buffer.
+wavefront (256 rounds), 2,048,576 task executions per step.  One step = for
+each graph: re-arm its state (join words, counts, digests, queues, sources),
+run the persistent scheduler until every task ran, finalise the status.
+Graph inputs are resident in HBM when the timed region starts; L2 (126 MB)
+is flushed between timed steps by writing a 512 MB buffer.
+
+Measured in the same run and reported beside it:
+  batched   4,096 motif graphs (33M tasks) in one CUDA-graph-captured
+            persistent launch, autotuned, versus one launch + sync per graph
+  serving   Poisson request streams at 1k / 10k / 50k requests/s through the
+            resident scheduler (p50 / p99 latency, tasks/s) versus serving the
+            same stream one launch per request
+  e2e       the headline workload through the C-ABI with host buffers:
+            ingest + validate + pack + upload, run, download every result
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+                  [--small] [--skip-batched] [--skip-serving]
 
---impl reference times the oracle (the sequential CPU executor) on the same
-workload, as the comparison arm.  Prints ONE JSON line.
+--impl reference times the oracle (the sequential CPU executor) on the
+headline workload, as the comparison arm.  Prints ONE JSON line.
 """
 from __future__ import annotations
 
@@ -36,9 +44,11 @@ import workloads as w  # noqa: E402
 METRIC = "tasks/s and ns/task overhead, batched vs plain per-graph; serving p50/p99"
 UNIT = "tasks/s"
 WORKLOAD = "large static DAGs, plain form: layered 1000x1000 (d~U{1..8}, R=16) + wavefront 1024x1024 (R=256)"
-
-
 SMALL = False   # --small: the same two shapes at reduced size (for profiler captures)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
 
 
 def _graphs():
@@ -67,8 +77,8 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", "0", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", os.environ.get("LOCAL_RANK", "0"),
+                                          f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -108,7 +118,7 @@ class ClockSampler:
 
 
 def _cpu_baseline(graphs):
-    """The oracle as it stands, one host core, over the whole workload."""
+    """The oracle as it stands, one host core, over the whole headline workload."""
     import oracle
     t0 = time.perf_counter()
     execs = 0
@@ -118,16 +128,14 @@ def _cpu_baseline(graphs):
         execs += r.execs
     dt = time.perf_counter() - t0
     return {"value": execs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"full workload ({execs} executions) on 1 host core, {dt:.2f} s"}
+            "sample": f"full headline workload ({execs} executions) on 1 host core, {dt:.2f} s"}
 
 
 def run_reference(args):
     graphs = _graphs()
-    for _ in range(args.warmup):
-        pass
     times = []
     cb = None
-    for i in range(args.steps):
+    for _ in range(args.steps):
         cb = _cpu_baseline(graphs)
         times.append(sum(g.n for g in graphs) / cb["value"])
     execs = sum(g.n for g in graphs)
@@ -139,6 +147,179 @@ def run_reference(args):
                       "data": "synthetic", "config": {"workload": WORKLOAD},
                       "cpu_baseline": cb,
                       "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(g):
+    """Graph metadata a task execution must touch: its 32-byte record read,
+    8 bytes of count/digest and 4 bytes of output written, and per successor
+    the 4-byte id read plus the 8-byte join word read and written."""
+    return 44 * g.n + 20 * g.m
+
+
+def headline(ex, graphs, args, torch, B):
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = ex.stream
+    handles = [ex.graph(g) for g in graphs]
+
+    def step():
+        for h in handles:
+            st = B.tg_submit(ex.ctx, h.handle)[0]
+            if st != 0:
+                raise B.TgError(st, "tg_submit")
+
+    for _ in range(args.warmup):
+        step()
+        torch.cuda.synchronize()
+    step_ms = []
+    with ClockSampler() as clk:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+    # scheduler-kernel time per graph (events around the kernel, same stream)
+    per_graph = {}
+    for h, g in zip(handles, graphs):
+        ts = []
+        for _ in range(3):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            assert ex.run(h) == 0
+            ts.append(ex.stats()["kernel_ns"])
+        per_graph[g.name] = statistics.median(ts)
+        out, cnt, dig, execs = ex.result(h)
+        assert execs == g.n and (cnt == 1).all()
+    stats = ex.stats()
+    for h in handles:
+        h.destroy()
+    return step_ms, per_graph, clk.summary(), stats
+
+
+def e2e(ex, graphs, reps):
+    ms = []
+    h2d = d2h = 0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for g in graphs:
+            gh = ex.graph(g)
+            assert ex.run(gh) == 0
+            ex.result(gh)
+            # copied per graph: successor lists + sources + record image, chunk
+            # table, descriptor; back: outputs and the 32-byte records
+            h2d += g.m * 4 + g.n * 4 + 32 * g.n + 64 + ((g.n + 255) // 256) * 4
+            d2h += g.n * 4 + g.n * 32
+            gh.destroy()
+        ms.append(1000 * (time.perf_counter() - t0))
+    return statistics.mean(ms), h2d, d2h
+
+
+def batched(Executor, torch):
+    """4,096 graphs in one autotuned, CUDA-graph-captured launch vs one launch each."""
+    t0 = time.time()
+    gs = w.config4()
+    gen_s = time.time() - t0
+    with Executor(arena_bytes=8 << 30, max_nodes=40_000_000, max_edges=450_000_000) as ex:
+        hs = [ex.graph(g) for g in gs]
+        b = ex.batch(hs)
+        b.launch()
+        st, sts = b.wait()
+        assert st == 0 and (sts == 0).all()
+        execs = ex.stats()["tasks"]
+        t1 = time.time()
+        chosen, tuned_ns = b.autotune(trials=2)
+        tune_s = time.time() - t1
+        ms = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(ex.stream)
+            b.launch()
+            e1.record(ex.stream)
+            st, sts = b.wait()
+            assert st == 0
+            ms.append(e0.elapsed_time(e1))
+        rounds = 0
+        for g, h in zip(gs, hs):
+            _, cnt, _, _ = ex.result(h)
+            rounds += int((cnt.astype(np.int64) * (g.params & 0xFFFF).astype(np.int64)).sum())
+        # payload-only ceiling at the same mean rounds per execution
+        mean_r = max(1, int(round(rounds / execs)))
+        pay_ns, _ = ex.bench_payload(int(execs), mean_r)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for h in hs:
+            assert ex.run(h) == 0
+        plain_s = time.perf_counter() - t1
+        b.destroy()
+    best_ms = min(ms)
+    return {"workload": "4096 motif graphs, n log-uniform [16, 65536], 5% loop conditions, rounds U{8..512}",
+            "graphs": len(gs), "tasks": int(sum(g.n for g in gs)), "executions": int(execs),
+            "batched_ms": best_ms, "batched_tasks_s": execs / (best_ms / 1000),
+            "plain_s": plain_s, "plain_tasks_s": execs / plain_s,
+            "batched_over_plain": (execs / (best_ms / 1000)) / (execs / plain_s),
+            "ns_per_task_overhead": (best_ms * 1e6 - pay_ns) / execs,
+            "payload_only_ms": pay_ns / 1e6, "payload_only_frac": (pay_ns / 1e6) / best_ms,
+            "mean_rounds": mean_r,
+            "autotuned": {k: chosen[k] for k in ("worker_blocks", "warps_per_block", "deque_depth",
+                                                 "steal_policy", "max_steal", "max_thieves")},
+            "autotune_s": tune_s, "generate_s": gen_s}
+
+
+def serving(Executor, torch):
+    """Poisson request streams through the resident scheduler vs one launch per request."""
+    P = 64
+    gs = [w.config5_request(i) for i in range(P)]
+    rng = np.random.default_rng(5)
+    out = {"workload": f"{P} request graphs of the serving generator (n log-uniform [64, 262144], "
+                       f"5% loop conditions, 64 rounds), request i runs graph i mod {P}",
+           "templates": P, "mean_tasks": float(np.mean([g.n for g in gs])), "lambdas": []}
+    with Executor(arena_bytes=16 << 30, max_nodes=80_000_000, max_edges=400_000_000,
+                  mem_budget_bytes=64 << 30) as ex:
+        ts = [ex.graph(g) for g in gs]
+        execs = []
+        for t in ts:
+            assert ex.run(t) == 0
+            execs.append(ex.result(t)[3])
+        execs = np.array(execs, np.float64)
+        for lam, count in ((1000, 5000), (10000, 20000), (50000, 20000)):
+            which = (np.arange(count) % P).astype(np.uint32)
+            arr = np.cumsum(rng.exponential(1e9 / lam, count)).astype(np.uint64)
+            ex.serve_start(time_limit_ns=120_000_000_000)
+            t1 = time.perf_counter()
+            st, lat, sts, peak, _ = ex.serve_replay(ts, which, arr)
+            wall = time.perf_counter() - t1
+            assert ex.serve_stop() == 0 and st == 0 and (sts == 0).all()
+            out["lambdas"].append({"req_per_s": lam, "requests": count, "p50_ms": float(np.percentile(lat, 50) / 1e6),
+                                   "p99_ms": float(np.percentile(lat, 99) / 1e6),
+                                   "tasks_s": float(execs[which].sum() / wall), "max_in_flight": int(peak)})
+        # the plain form: one launch + sync per request, in arrival order
+        count = 600
+        which = (np.arange(count) % P).astype(np.uint32)
+        arr = np.cumsum(rng.exponential(1e9 / 1000, count))
+        lat = []
+        t1 = time.perf_counter()
+        for r in range(count):
+            now = (time.perf_counter() - t1) * 1e9
+            if now < arr[r]:
+                time.sleep((arr[r] - now) / 1e9)
+            assert ex.run(ts[which[r]]) == 0
+            lat.append((time.perf_counter() - t1) * 1e9 - arr[r])
+        wall = time.perf_counter() - t1
+        lat = np.array(lat)
+        out["plain_1k"] = {"req_per_s": 1000, "requests": count, "p50_ms": float(np.percentile(lat, 50) / 1e6),
+                           "p99_ms": float(np.percentile(lat, 99) / 1e6),
+                           "tasks_s": float(execs[which].sum() / wall)}
+        out["p99_plain_over_served_1k"] = out["plain_1k"]["p99_ms"] / out["lambdas"][0]["p99_ms"]
+    return out
 
 
 def run_b300(args):
@@ -158,44 +339,7 @@ def run_b300(args):
     peaks, peak_kind = _peaks()
 
     ex = Executor(arena_bytes=(512 << 20) if SMALL else (4 << 30))
-    handles = [ex.graph(g) for g in graphs]
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    stream = ex.stream
-
-    def step():
-        for h in handles:
-            st = B.tg_submit(ex.ctx, h.handle)[0]
-            if st != 0:
-                raise B.TgError(st, "tg_submit")
-
-    # warm-up
-    for _ in range(args.warmup):
-        step()
-        torch.cuda.synchronize()
-
-    kern_ns = []
-    step_ms = []
-    with ClockSampler() as clk:
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            kern_ns.append(ex.stats()["kernel_ns"])   # scheduler kernel of the last graph
-        torch.cuda.synchronize()
-    statuses = []
-    for h in handles:
-        # re-run once more and read statuses / results for a sanity check
-        statuses.append(ex.run(h))
-    assert all(s == 0 for s in statuses), statuses
+    step_ms, per_graph, clocks, stats = headline(ex, graphs, args, torch, B)
     tot_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([tot_ms], device="cuda")
@@ -204,50 +348,25 @@ def run_b300(args):
     ms_per_step = tot_ms / args.steps
     value = execs_per_step * world / (ms_per_step / 1000.0)
 
-    # per-graph kernel time of the scheduler (events inside the library, same stream)
-    per_graph = {}
-    for h, g in zip(handles, graphs):
-        ts = []
-        for _ in range(3):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            assert ex.run(h) == 0
-            ts.append(ex.stats()["kernel_ns"])
-        per_graph[g.name] = statistics.median(ts)
+    # roofline of the dominant kernel (the scheduler): graph-metadata bytes
+    # per launch over its average launch time, against the measured HBM copy
+    # bandwidth; beside it the integer-ALU view and the atomic ceiling
     sched_ns = sum(per_graph.values())
+    n_launch = len(graphs)
+    alg_bytes = sum(algorithmic_bytes(g) for g in graphs)
+    achieved_gbs = (alg_bytes / n_launch) / (sched_ns / n_launch * 1e-9) / 1e9
     rounds_total = sum(int((g.params & 0xFFFF).astype(np.int64).sum()) for g in graphs)
-    int_ops = 9 * rounds_total
-    # integer-ALU peak: 148 SMs x 64 INT32 lanes per clock x max SM clock
     alu_peak = 148 * 64 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-    achieved = int_ops / (sched_ns * 1e-9) / 1e12
-    # measured payload-only ceiling on the same execution multiset
+    alu_achieved = 9 * rounds_total / (sched_ns * 1e-9) / 1e12
     pay_ns = 0
     for g in graphs:
-        R = int(g.params[0] & 0xFFFF)
-        ns, _ = ex.bench_payload(g.n, R)
+        ns, _ = ex.bench_payload(g.n, int(g.params[0] & 0xFFFF))
         pay_ns += ns
-    # critical-path floor: longest chain x payload latency per task is
-    # reported by the payload kernel's one-task-per-lane timing
-    stats = ex.stats()
-
-    # end to end through the C-ABI with host buffers: ingest + pack + H2D,
-    # run, D2H of every task's out/cnt/dig
-    e2e_ms = []
-    h2d = d2h = 0
-    for _ in range(max(1, min(args.steps, 3))):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h2d = d2h = 0
-        for g in graphs:
-            gh = ex.graph(g)
-            st = ex.run(gh)
-            out, cnt, dig, _ = ex.result(gh)
-            assert st == 0
-            h2d += g.n * 36 + (g.m + 1) * 4 + 64
-            d2h += g.n * 36
-            gh.destroy()
-        e2e_ms.append(1000 * (time.perf_counter() - t0))
-    e2e_val = execs_per_step / (statistics.mean(e2e_ms) / 1000.0)
+    atom_ns = ex.bench_atomics(1 << 26, 1 << 24)
+    atom_ceiling = (1 << 26) / (atom_ns * 1e-9)
+    atomics_per_launch = sum(g.m + 2 * g.n for g in graphs)   # releases + in-flight flag + re-arm
+    e2e_ms, h2d, d2h = e2e(ex, graphs, max(1, min(args.steps, 3)))
+    ex.close()
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -256,23 +375,31 @@ def run_b300(args):
         "config": {"workload": WORKLOAD, "graphs": [g.name for g in graphs], "tasks_per_step": execs_per_step,
                    "l2": "flushed between steps (512 MB write)", "worker_blocks": stats["worker_blocks"],
                    "warps_per_block": stats["warps_per_block"]},
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": statistics.mean(e2e_ms)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                     "frac": achieved / alu_peak, "traffic": None,
-                     "note": "scheduler kernel; peak = 148 SM x 64 INT32 lanes x max clock (derived)"},
-        "payload_only": {"ns": pay_ns, "sched_ns": sched_ns, "per_graph_sched_ns": per_graph,
-                         "ns_per_task_overhead": (sched_ns - pay_ns) / execs_per_step},
+        "e2e": {"value": execs_per_step / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks.get("hbm_gbs", 6400.0),
+                     "unit": "GB/s", "frac": achieved_gbs / peaks.get("hbm_gbs", 6400.0), "traffic": None,
+                     "peak_kind": peak_kind,
+                     "note": "scheduler kernel; graph metadata 44 B/task + 20 B/edge per launch; the kernel is "
+                             "bound by the dependency chain (one scheduling step per level), not by bandwidth"},
+        "alu": {"achieved_tops": alu_achieved, "peak_tops": alu_peak, "frac": alu_achieved / alu_peak,
+                "payload_only_ms": pay_ns / 1e6, "sched_ms": sched_ns / 1e6,
+                "ns_per_task_overhead": (sched_ns - pay_ns) / execs_per_step},
+        "atomics": {"ceiling_per_s": atom_ceiling, "achieved_per_s": atomics_per_launch / (sched_ns * 1e-9),
+                    "frac": atomics_per_launch / (sched_ns * 1e-9) / atom_ceiling},
+        "per_graph_sched_ms": {k: v / 1e6 for k, v in per_graph.items()},
+        "scheduler_stats": {k: stats[k] for k in ("steal_attempts", "steal_hits", "spills", "warp_iters",
+                                                  "pops_hand", "pops_local")},
         "gpu_launches": 3 * len(graphs) * args.steps,
-        "peaks": peak_kind,
+        "clocks": clocks,
     }
-    with ClockSampler() as _c:
-        pass
-    line["clocks"] = clk.summary()
+    if not args.skip_batched and not SMALL:
+        line["batched"] = batched(Executor, torch)
+    if not args.skip_serving and not SMALL:
+        line["serving"] = serving(Executor, torch)
     if rank == 0:
         line["cpu_baseline"] = _cpu_baseline(graphs)
         print(json.dumps(line))
-    ex.close()
 
 
 def main():
@@ -283,6 +410,8 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--small", action="store_true",
                     help="layered 100x1000 + wavefront 256x256 (profiler captures; not a bench line)")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
     args = ap.parse_args()
     global SMALL
     SMALL = args.small
