@@ -81,11 +81,12 @@ enum {
 
 /* Option flags. */
 #define TG_OPT_NO_RACE_CHECK 0x1u   /* skip the per-activation in-flight check */
+#define TG_OPT_TRACE 0x2u           /* record per-task start / publish times (tg_trace_copy) */
 
 /* Context options; a zero field selects the default (in brackets). */
 typedef struct {
     int32_t worker_blocks;     /* persistent blocks [SMs x resident blocks per SM] */
-    int32_t warps_per_block;   /* worker warps per block [8] */
+    int32_t warps_per_block;   /* worker warps per block [16] */
     int32_t deque_depth;       /* entries of each block's public deque, power of 2 [4096] */
     int32_t steal_policy;      /* 0 random victims, 1 neighbour ring [0] */
     int32_t max_steal;         /* victims tried per steal round [8] */
@@ -93,6 +94,9 @@ typedef struct {
     uint32_t flags;            /* TG_OPT_* */
     uint32_t idle_sleep_ns;    /* wait of an idle warp that is not its block's thief [256] */
     int32_t max_thieves;       /* blocks allowed to steal / poll at the same time [16] */
+    int32_t batch_max;         /* activations a warp takes per step, 1..32 [32] */
+    int32_t local_keep;        /* ready activations a block keeps in shared memory before the
+                                  rest goes to its stealable deque, <= smem_ring [32] */
     int32_t reserved;
     uint64_t time_limit_ns;    /* device time limit per launch [10 s] */
     uint64_t exec_cap;         /* executions per graph before TG_ERR_EXEC_LIMIT [2^31] */
@@ -165,6 +169,9 @@ int tg_instance_create(tg_ctx *ctx, tg_graph *g, tg_graph **out);
  * and the resident kernel injects its sources while other graphs are running
  * -- and tg_poll / tg_wait read the completion records the kernel posts to
  * host-mapped memory.  tg_run and batches return TG_ERR_BUSY meanwhile.
+ * The server runs one block per SM, with the context's warps per block
+ * halved until two such blocks would fit on an SM, so that the copy kernels
+ * re-arming instances can run beside it.
  * time_limit_ns bounds the server's lifetime (0 = 60 s); a graph still in
  * flight at the limit ends with TG_ERR_TIMEOUT.  Admission by memory budget
  * is the caller's loop: tg_instance_create / tg_graph_create fail with
@@ -208,7 +215,8 @@ int tg_batch_launch(tg_ctx *ctx, tg_batch *b);
 int tg_batch_wait(tg_ctx *ctx, tg_batch *b, int *statuses);
 int tg_batch_destroy(tg_ctx *ctx, tg_batch *b);
 /* Autotune a batch (worker-block count, warps per block, deque depth, steal
- * policy, victims per steal round, thief slots): time its launch under
+ * policy, victims per steal round, thief slots, activations per warp step):
+ * time its launch under
  * candidate geometries by coordinate descent, `trials` timed launches each,
  * keep the fastest and re-capture the batch with it.  With cache_path
  * non-NULL, a result cached for the same device and batch shape (graph,
@@ -278,6 +286,12 @@ int tg_bench_atomics(tg_ctx *ctx, uint64_t count, uint64_t footprint_words, uint
 int tg_run_noalloc(uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
                    const uint32_t *succ_off, const uint32_t *succ, uint32_t n_edges, uint32_t seed,
                    uint32_t *out, uint32_t *cnt, uint32_t *dig, void *cuda_stream);
+
+/* With TG_OPT_TRACE: copy the device clock (ns, %globaltimer) at which each
+ * task of g last started its payload and last published its successors, for
+ * n entries each (start_ns / end_ns may be NULL).  TG_ERR_INVALID without the
+ * option. */
+int tg_trace_copy(tg_ctx *ctx, const tg_graph *g, uint64_t *start_ns, uint64_t *end_ns);
 
 const char *tg_strerror(int status);
 

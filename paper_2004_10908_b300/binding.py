@@ -19,6 +19,7 @@ TG_ERR_INVALID, TG_ERR_NO_SOURCE, TG_ERR_EDGE_KIND, TG_ERR_BUDGET = -1, -2, -3, 
 TG_ERR_RACE, TG_ERR_EXEC_LIMIT, TG_ERR_TIMEOUT, TG_ERR_CANCELLED = -5, -6, -7, -8
 TG_ERR_CUDA, TG_ERR_INTERNAL, TG_ERR_BUSY = -9, -10, -11
 TG_OPT_NO_RACE_CHECK = 0x1
+TG_OPT_TRACE = 0x2
 
 STATUS_NAMES = {TG_OK: "OK", TG_PENDING: "PENDING", TG_ERR_INVALID: "INVALID",
                 TG_ERR_NO_SOURCE: "NO_SOURCE", TG_ERR_EDGE_KIND: "EDGE_KIND", TG_ERR_BUDGET: "BUDGET",
@@ -38,7 +39,8 @@ class tg_ctx_opts(ctypes.Structure):
                 ("deque_depth", ctypes.c_int32), ("steal_policy", ctypes.c_int32),
                 ("max_steal", ctypes.c_int32), ("smem_ring", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("idle_sleep_ns", ctypes.c_uint32),
-                ("max_thieves", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_thieves", ctypes.c_int32), ("batch_max", ctypes.c_int32),
+                ("local_keep", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("time_limit_ns", ctypes.c_uint64), ("exec_cap", ctypes.c_uint64),
                 ("mem_budget_bytes", ctypes.c_uint64), ("max_nodes", ctypes.c_uint64),
                 ("max_edges", ctypes.c_uint64)]
@@ -97,6 +99,7 @@ SIGNATURES = {
     "tg_bench_payload": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "tg_bench_atomics": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(_u64)]),
     "tg_run_noalloc": (ctypes.c_int, [_u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]),
+    "tg_trace_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "tg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -307,3 +310,11 @@ def tg_run_noalloc(n_nodes, kinds_ptr, params_ptr, succ_off_ptr, succ_ptr, n_edg
     return load().tg_run_noalloc(n_nodes, _vp(kinds_ptr), _vp(params_ptr), _vp(succ_off_ptr), _vp(succ_ptr),
                                  n_edges, seed & 0xFFFFFFFF, _vp(out_ptr), _vp(cnt_ptr), _vp(dig_ptr),
                                  _vp(cuda_stream))
+
+
+def tg_trace_copy(ctx, g, n):
+    """(start_ns[n], end_ns[n]) of each task's last execution (TG_OPT_TRACE)."""
+    a = np.zeros(n, np.uint64)
+    b = np.zeros(n, np.uint64)
+    _check(load().tg_trace_copy(_vp(ctx), _vp(g), a.ctypes.data_as(_vp), b.ctypes.data_as(_vp)), "tg_trace_copy")
+    return a, b

@@ -26,7 +26,7 @@ constexpr u32 kSubRing = 1u << 16;  // server-mode submission / completion ring 
 // keeps the one it was captured with), within what the context allocated.
 struct Geometry {
     int blocks = 0, threads = 0;
-    u32 ring = 0, depth = 0, policy = 0, max_steal = 0, thieves = 0, idle_ns = 0;
+    u32 ring = 0, depth = 0, policy = 0, max_steal = 0, thieves = 0, idle_ns = 0, batch = 32, keep = 0;
 };
 
 u64 now_ns()
@@ -158,6 +158,7 @@ struct tg_ctx {
     u32 *outv = nullptr;
     u32 *chunk_gid = nullptr;
     u32 *edges = nullptr;
+    u64 *trace = nullptr;          // TG_OPT_TRACE buffer (2 words per task)
     cudaStream_t side = nullptr;   // instance set-up and server submissions
     SubEntry *sub = nullptr;       // device submission ring
     SubEntry *h_sub = nullptr;     // pinned staging of submission entries
@@ -224,10 +225,13 @@ KParams base_params(tg_ctx *c, const Geometry &g)
     p.node_cap = (u32)c->node_cap;
     p.idle_sleep_ns = g.idle_ns;
     p.max_thieves = g.thieves;
+    p.batch_max = g.batch;
+    p.local_keep = g.keep;
     p.thief_slots = c->thief_slots;
     p.time_limit_ns = c->opts.time_limit_ns;
     p.cancel = c->d_cancel;
     p.status_out = c->d_status;
+    p.trace = c->trace;
     p.sub = c->sub;
     p.sub_mask = kSubRing - 1u;
     p.comp_mask = kSubRing - 1u;
@@ -283,12 +287,13 @@ int clear_if_dirty(tg_ctx *c)
 // occupancy of the scheduler kernel at that block shape.
 int resolve_geometry(const tg_ctx *c, const tg_ctx_opts &o, Geometry &g)
 {
-    const int warps = o.warps_per_block > 0 ? o.warps_per_block : 8;
+    const int warps = o.warps_per_block > 0 ? o.warps_per_block : 16;
     const u32 ring = o.smem_ring > 0 ? (u32)o.smem_ring : 1024u;
     const u32 depth = o.deque_depth > 0 ? (u32)o.deque_depth : c->dq_cap;
     if (warps > 32 || !is_pow2(ring) || ring < 64 || ring > 8192 || !is_pow2(depth) || depth < 64 ||
         depth > c->dq_cap || o.steal_policy < 0 || o.steal_policy > 1 || o.max_thieves > 1024 ||
-        o.max_steal < 0 || o.worker_blocks < 0)
+        o.max_steal < 0 || o.worker_blocks < 0 || o.batch_max < 0 || o.batch_max > 32 || o.local_keep < 0 ||
+        (u32)o.local_keep > ring)
         return TG_ERR_INVALID;
     int per_sm = 0;
     if (sched_occupancy(warps * 32, sched_dyn_smem(ring, (u32)warps), &per_sm) != cudaSuccess || per_sm <= 0)
@@ -302,6 +307,10 @@ int resolve_geometry(const tg_ctx *c, const tg_ctx_opts &o, Geometry &g)
     g.max_steal = o.max_steal > 0 ? (u32)o.max_steal : 8u;
     g.thieves = o.max_thieves > 0 ? (u32)o.max_thieves : 16u;
     g.idle_ns = o.idle_sleep_ns > 0 ? o.idle_sleep_ns : 256u;
+    g.batch = o.batch_max > 0 ? (u32)o.batch_max : 32u;
+    // a short shared-memory backlog: ready work beyond it goes to the block's
+    // public deque where idle warps of other blocks can take it
+    g.keep = std::min<u32>(o.local_keep > 0 ? (u32)o.local_keep : 32u, ring);
     return TG_OK;
 }
 
@@ -315,6 +324,8 @@ void geometry_to_opts(const Geometry &g, tg_ctx_opts &o)
     o.smem_ring = (int32_t)g.ring;
     o.max_thieves = (int32_t)g.thieves;
     o.idle_sleep_ns = g.idle_ns;
+    o.batch_max = (int32_t)g.batch;
+    o.local_keep = (int32_t)g.keep;
 }
 
 }  // namespace
@@ -407,7 +418,7 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
     if (ncap == 0) {
         // per task: 36 B execution range + 8 B of injection queue + 32 B
         // pristine image + successors (about 8 x 4 B) in the edge pool
-        ncap = (rest / 128) & ~(u64)255;
+        ncap = (rest / ((o.flags & TG_OPT_TRACE) ? 144 : 128)) & ~(u64)255;
         if (ncap > kMaxNodeIndex)
             ncap = kMaxNodeIndex & ~(u64)255;
     }
@@ -416,7 +427,7 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
         return TG_ERR_INVALID;
     }
     u64 icap = next_pow2(ncap + 4096);
-    size_t fixed = (size_t)ncap * (sizeof(NodeSlot) + 8) + (size_t)icap * 8 + 1024;
+    size_t fixed = (size_t)ncap * (sizeof(NodeSlot) + 8 + ((o.flags & TG_OPT_TRACE) ? 16 : 0)) + (size_t)icap * 8 + 4096;
     if (fixed >= rest) {
         delete c;
         return TG_ERR_INVALID;
@@ -428,6 +439,8 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
         return TG_ERR_INVALID;
     }
     c->inj = (u64 *)take((size_t)icap * 8);
+    if (o.flags & TG_OPT_TRACE)
+        c->trace = (u64 *)take((size_t)ncap * 16);
     c->slots = (NodeSlot *)take((size_t)ncap * sizeof(NodeSlot));
     c->outv = (u32 *)take((size_t)ncap * 4);
     c->chunk_gid = (u32 *)take((size_t)(ncap >> kChunkShift) * 4 + 256);
@@ -1189,9 +1202,9 @@ int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache
                     continue;
                 tg_ctx_opts o{};
                 unsigned long long t = 0;
-                if (std::sscanf(tab + 1, "%d %d %d %d %d %d %d %u %llu", &o.worker_blocks, &o.warps_per_block,
-                                &o.deque_depth, &o.steal_policy, &o.max_steal, &o.max_thieves, &o.smem_ring,
-                                &o.idle_sleep_ns, &t) == 9) {
+                if (std::sscanf(tab + 1, "%d %d %d %d %d %d %d %u %d %d %llu", &o.worker_blocks,
+                                &o.warps_per_block, &o.deque_depth, &o.steal_policy, &o.max_steal, &o.max_thieves,
+                                &o.smem_ring, &o.idle_sleep_ns, &o.batch_max, &o.local_keep, &t) == 11) {
                     Geometry g;
                     if (resolve_geometry(c, o, g) == TG_OK) {
                         best = o;
@@ -1238,6 +1251,8 @@ int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache
         const int policy_c[] = {0, 1};
         const int steal_c[] = {2, 8, 32};
         const int thief_c[] = {8, 16, 64};
+        const int batch_c[] = {8, 16, 32};
+        const int keep_c[] = {16, 32, 128, 512};
         auto try_knob = [&](auto setter, const int *vals, int nv) -> int {
             for (int i = 0; i < nv; ++i) {
                 tg_ctx_opts o = best;
@@ -1267,13 +1282,16 @@ int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache
             (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.deque_depth = v; }, depth_c, 2)) != TG_OK ||
             (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.steal_policy = v; }, policy_c, 2)) != TG_OK ||
             (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.max_steal = v; }, steal_c, 3)) != TG_OK ||
-            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.max_thieves = v; }, thief_c, 3)) != TG_OK)
+            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.max_thieves = v; }, thief_c, 3)) != TG_OK ||
+            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.batch_max = v; }, batch_c, 3)) != TG_OK ||
+            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.local_keep = v; }, keep_c, 4)) != TG_OK)
             return rc2;
         if (cache_path) {
             if (FILE *f = std::fopen(cache_path, "a")) {
-                std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %llu\n", key.c_str(), best.worker_blocks,
+                std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %d %d %llu\n", key.c_str(), best.worker_blocks,
                              best.warps_per_block, best.deque_depth, best.steal_policy, best.max_steal,
-                             best.max_thieves, best.smem_ring, best.idle_sleep_ns, (unsigned long long)best_t);
+                             best.max_thieves, best.smem_ring, best.idle_sleep_ns, best.batch_max, best.local_keep,
+                             (unsigned long long)best_t);
                 std::fclose(f);
             }
         }
@@ -1467,12 +1485,20 @@ int tg_serve_start(tg_ctx *c, uint64_t time_limit_ns)
     if (rc != TG_OK)
         return rc;
     Geometry g = c->geo;
+    // one block per SM, of a shape of which two would fit: the resident
+    // server leaves room on every SM for the copy kernels that re-arm
+    // instances (device-to-device record copies)
     int per_sm = 0;
-    if (sched_occupancy(g.threads, sched_dyn_smem(g.ring, (u32)(g.threads / 32)), &per_sm, true) != cudaSuccess ||
-        per_sm <= 0)
+    for (;;) {
+        if (sched_occupancy(g.threads, sched_dyn_smem(g.ring, (u32)(g.threads / 32)), &per_sm, true) !=
+            cudaSuccess)
+            return TG_ERR_CUDA;
+        if (per_sm >= 2 || g.threads <= 64)
+            break;
+        g.threads /= 2;
+    }
+    if (per_sm < 2)
         return TG_ERR_CUDA;
-    // one block per SM: the resident server leaves room on every SM for the
-    // copy kernels that re-arm instances (device-to-device record copies)
     g.blocks = std::min(g.blocks, std::min(c->sm_count, kMaxBlocks));
     c->serve_geo = g;
     *(volatile u32 *)c->h_stop = 0u;
@@ -1629,3 +1655,19 @@ extern "C" int tg_serve_replay(tg_ctx *c, tg_graph *const *templates, uint32_t n
     return first_err;
 }
 
+
+extern "C" int tg_trace_copy(tg_ctx *c, const tg_graph *g, uint64_t *start_ns, uint64_t *end_ns)
+{
+    if (!c || !g || g->ctx != c || !c->trace)
+        return TG_ERR_INVALID;
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<u64> h((size_t)g->n * 2);
+    TG_CUDA(cudaMemcpy(h.data(), c->trace + 2 * g->node_off, h.size() * 8, cudaMemcpyDeviceToHost));
+    for (u32 v = 0; v < g->n; ++v) {
+        if (start_ns)
+            start_ns[v] = h[2 * (size_t)v];
+        if (end_ns)
+            end_ns[v] = h[2 * (size_t)v + 1];
+    }
+    return TG_OK;
+}

@@ -126,9 +126,12 @@ struct KParams {
     u32 idle_sleep_ns;     // wait of a non-thief idle warp
     u32 max_thieves;       // thief slots (blocks stealing / polling at once)
     u32 dq_stride;         // entries allocated per block deque (>= dq_mask + 1)
-    u32 pad3;
+    u32 batch_max;         // activations a warp takes per step (1..32)
+    u32 local_keep;        // shared-memory ring size above which new work goes public (0 = default)
+    u32 pad4;
     u32 *thief_slots;      // max_thieves words, each on its own 128-byte line
     u64 time_limit_ns;
+    u64 *trace;            // TG_OPT_TRACE: per task {start ns, publish ns} (may be null)
     volatile u32 *cancel;  // host-mapped cancel flag (may be null)
     i32 *status_out;       // host-mapped per-gid statuses (may be null)
     // server mode

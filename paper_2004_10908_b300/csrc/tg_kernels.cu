@@ -13,6 +13,8 @@
 //     overflow.
 // All rings are multi-producer multi-consumer with monotonically increasing
 // 32-bit tickets and an EMPTY marker per slot; every wait is bounded.
+#include <mutex>
+
 #include "tg_internal.h"
 #include "../../include/tg.h"
 
@@ -24,7 +26,7 @@ constexpr int kSpinLimit = 1 << 20;     // bounded waits on a slot (iterations)
 constexpr int kCasTries = 256;
 constexpr u32 kStage = 256;             // staged activations per warp (shared memory)
 constexpr int kRelUnroll = 4;           // successor releases in flight per lane
-constexpr u32 kPerLaneMax = 16;         // widest fan-out released lane by lane
+constexpr u32 kPerLaneMax = 4;          // widest fan-out released lane by lane (one round)
 constexpr u32 kHandMax = 2;             // narrowest step output kept by the warp itself
 
 // ---------------------------------------------------------------------------
@@ -128,7 +130,7 @@ struct Ring {
 
 // Warp-cooperative pop into lanes [0, k).  A thief takes half of what it
 // sees (at least one); an owner takes up to 32.
-__device__ __forceinline__ int ring_pop(const Ring &r, bool thief, int lane, u64 &e, int &err)
+__device__ __forceinline__ int ring_pop(const Ring &r, bool thief, int lane, u64 &e, int &err, int want = 32)
 {
     u32 h = 0;
     int k = 0;
@@ -138,7 +140,7 @@ __device__ __forceinline__ int ring_pop(const Ring &r, bool thief, int lane, u64
             int avail = (int)(tt - hh);
             if (avail <= 0)
                 break;
-            int kk = thief ? min(32, (avail + 1) >> 1) : min(32, avail);
+            int kk = thief ? min(want, (avail + 1) >> 1) : min(want, avail);
             if (atomicCAS(r.head, hh, hh + (u32)kk) == hh) {
                 h = hh;
                 k = kk;
@@ -215,7 +217,9 @@ struct WarpCtx {
     Ring local;      // block's shared-memory ring
     Ring own;        // block's public deque
     Ring inj;        // shared injection queue
-    u32 high_water;  // local ring size above which new work goes public
+    u32 high_water;  // local ring size above which new work goes public while a block is hungry
+    u32 keep_hi;     // local ring size above which new work always goes public
+    const u32 *hungry;  // blocks whose thief found no work anywhere
     u32 *avail_word; // this block's word / bit in the work-available bitmap
     u32 avail_bit;
     int err;
@@ -226,11 +230,15 @@ __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u6
 {
     if (__ballot_sync(kFull, has) == 0)
         return;
-    u32 lsz = 0;
-    if (lane == 0)
-        lsz = ring_size(w.local);
-    lsz = __shfl_sync(kFull, lsz, 0);
-    bool pub = has && lsz >= w.high_water;
+    // spill beyond a short backlog while some block is idle, beyond a long
+    // one otherwise (the hungry count is read only past the short mark)
+    int spill = 0;
+    if (lane == 0) {
+        const u32 lsz = ring_size(w.local);
+        spill = lsz >= w.keep_hi || (lsz >= w.high_water && (i32)vld32(w.hungry) > 0);
+    }
+    spill = __shfl_sync(kFull, spill, 0);
+    bool pub = has && spill;
     bool loc = has && !pub;
     if (!ring_push(w.local, loc, ent, lane, w.err))
         pub = pub || loc;
@@ -322,7 +330,7 @@ __global__ void sched_kernel(KParams p)
     __shared__ u32 s_push[32 * 32];
     __shared__ u32 s_keep[32 * 32];
     __shared__ u64 s_stats[ST_COUNT];
-    __shared__ int s_thief, s_stop;
+    __shared__ int s_thief, s_stop, s_hungry;
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -336,10 +344,12 @@ __global__ void sched_kernel(KParams p)
         s_tail = 0;
         s_thief = 0;
         s_stop = 0;
+        s_hungry = 0;
     }
     __syncthreads();
 
     const bool race_check = (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
+    const int bmax = (int)min(32u, max(1u, p.batch_max));
     const bool single = !kServe && p.lt == nullptr;   // one graph: every activation has gid == single_gid
     const u32 single_cap = single ? ld_imm<kServe>(&p.descs[p.single_gid].exec_cap) : 0u;
     const u64 t0 = globaltimer();
@@ -350,9 +360,12 @@ __global__ void sched_kernel(KParams p)
     w.own = Ring{&p.dqc[blockIdx.x].head, &p.dqc[blockIdx.x].tail,
                  p.dq + (size_t)blockIdx.x * p.dq_stride, p.dq_mask};
     w.inj = Ring{&p.ctl->inj.head, &p.ctl->inj.tail, p.inj, p.inj_mask};
-    // keep locally what the block's warps can take at once; beyond that,
-    // new activations go to the public deque where other blocks steal them
-    w.high_water = min(ring_n / 2u, max(64u, (blockDim.x / 32u) * 32u));
+    // a short shared-memory backlog while other blocks are idle (beyond it,
+    // new activations go to the public deque where their thieves steal
+    // them), half the ring while none is
+    w.high_water = min(p.local_keep ? p.local_keep : 32u, ring_n);
+    w.keep_hi = max(w.high_water, ring_n / 2u);
+    w.hungry = &p.ctl->hungry;
     w.err = 0;
     w.avail_word = &p.ctl->avail[blockIdx.x >> 5];
     w.avail_bit = 1u << (blockIdx.x & 31u);
@@ -387,7 +400,7 @@ __global__ void sched_kernel(KParams p)
             nh = 0;
             st_hand++;
         } else {
-            k = ring_pop(w.local, false, lane, e, w.err);
+            k = ring_pop(w.local, false, lane, e, w.err, bmax);
             if (k) {
                 st_local++;
             } else {
@@ -485,11 +498,11 @@ __global__ void sched_kernel(KParams p)
                             emit(w, h, ent, lane, st_spill);
                         }
                         st_inj++;
-                        k = ring_pop(w.local, false, lane, e, w.err);
+                        k = ring_pop(w.local, false, lane, e, w.err, bmax);
                     }
                 }
                 if (k == 0)
-                    k = ring_pop(w.own, false, lane, e, w.err);
+                    k = ring_pop(w.own, false, lane, e, w.err, bmax);
                 if (k) {
                     st_own++;
                 } else {
@@ -528,7 +541,7 @@ __global__ void sched_kernel(KParams p)
                                         p.dq_mask};
                                 st_try++;
                                 tries++;
-                                k = ring_pop(vr, true, lane, e, w.err);
+                                k = ring_pop(vr, true, lane, e, w.err, bmax);
                                 if (k) {
                                     st_hit++;
                                 } else if (lane == 0) {
@@ -542,7 +555,7 @@ __global__ void sched_kernel(KParams p)
                         }
                     }
                     if (k == 0) {
-                        k = ring_pop(w.inj, true, lane, e, w.err);
+                        k = ring_pop(w.inj, true, lane, e, w.err, bmax);
                         if (k)
                             st_inj++;
                     }
@@ -568,6 +581,8 @@ __global__ void sched_kernel(KParams p)
                         }
                         if (stop)
                             *(volatile int *)&s_stop = 1;
+                        else if (atomicExch(&s_hungry, 1) == 0)
+                            atomicAdd(&p.ctl->hungry, 1u);
                         vst32(&p.thief_slots[my_slot * 32u], 0u);
                         __threadfence_block();
                         *(volatile int *)&s_thief = 0;
@@ -587,6 +602,8 @@ __global__ void sched_kernel(KParams p)
             }
         }
         st_iters++;
+        if (lane == 0 && *(volatile int *)&s_hungry != 0 && atomicExch(&s_hungry, 0) == 1)
+            atomicSub(&p.ctl->hungry, 1u);
 
         // ---- read the activations' tasks
         bool act = lane < k && (u32)e != kEmpty32;
@@ -695,6 +712,8 @@ __global__ void sched_kernel(KParams p)
         if (act && strong)
             atomicAdd(&p.slots[u].W, (u64)indeg - ((u64)insum << 32));
 
+        if (p.trace && act)
+            p.trace[2ull * u] = globaltimer();
         // ---- payload
         const u32 x = act ? task_payload(lid, iter, insum, rounds) : 0u;
         const u32 dg = mix32(stt.y ^ x);
@@ -799,16 +818,22 @@ __global__ void sched_kernel(KParams p)
                 }
             }
         } else {
+            // software-pipelined rounds: while a round's join-word atomics are
+            // in flight the previous round's race checks are examined, and the
+            // next round's successor ids are fetched before this round stages
+            u32 pfl_[kRelUnroll], pgo_[kRelUnroll];
+#pragma unroll
+            for (int j = 0; j < kRelUnroll; ++j) {
+                pfl_[j] = 0u;
+                pgo_[j] = 0u;
+            }
             for (u32 base = 0; base < total; base += 32u * kRelUnroll) {
-                if (base)
-                    fetch_flat(base);
-                u32 xo_[kRelUnroll], uo_[kRelUnroll], go_[kRelUnroll], fl_[kRelUnroll];
-                u64 old_[kRelUnroll];
+                u32 xo_[kRelUnroll], go_[kRelUnroll], fl_[kRelUnroll];
+                u64 old_[kRelUnroll], ent_[kRelUnroll];
                 bool has_[kRelUnroll];
 #pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j) {
                     xo_[j] = __shfl_sync(kFull, x, (int)ow_[j]);
-                    uo_[j] = __shfl_sync(kFull, u, (int)ow_[j]);
                     go_[j] = __shfl_sync(kFull, gid, (int)ow_[j]);
                     const int run_o = __shfl_sync(kFull, (int)run, (int)ow_[j]);   // every lane shuffles
                     v_[j] = v_[j] && run_o != 0;
@@ -817,27 +842,37 @@ __global__ void sched_kernel(KParams p)
                 for (int j = 0; j < kRelUnroll; ++j)
                     old_[j] = v_[j] ? atomicAdd(&p.slots[s_[j]].W, ((u64)xo_[j] << 32) - 1ull) : 0ull;
 #pragma unroll
+                for (int j = 0; j < kRelUnroll; ++j)
+                    if (pfl_[j] & kInflight)
+                        racy = pgo_[j];
+#pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j) {
+                    const u32 uo = __shfl_sync(kFull, u, (int)ow_[j]);
                     fl_[j] = 0u;
                     has_[j] = v_[j] && (u32)old_[j] == 1u;
                     if (has_[j]) {
                         atomicAdd(&my_push[ow_[j]], 1u);
                         if (race_check) {
-                            if (s_[j] == uo_[j])
+                            if (s_[j] == uo)
                                 my_keep[ow_[j]] = 1u;
                             else
                                 fl_[j] = atomicOr(&p.slots[s_[j]].cnt, kInflight);
                         }
                     }
+                    ent_[j] = ((u64)((u32)(old_[j] >> 32) + xo_[j]) << 32) | kStrongBit | (u64)s_[j];
+                    pfl_[j] = fl_[j];
+                    pgo_[j] = go_[j];
                 }
+                if (base + 32u * kRelUnroll < total)
+                    fetch_flat(base + 32u * kRelUnroll);
 #pragma unroll
-                for (int j = 0; j < kRelUnroll; ++j) {
-                    const u64 ent = ((u64)((u32)(old_[j] >> 32) + xo_[j]) << 32) | kStrongBit | (u64)s_[j];
-                    stage(w, my_stage, ns, has_[j], ent, lane, st_spill);
-                    if (fl_[j] & kInflight)
-                        racy = go_[j];
-                }
+                for (int j = 0; j < kRelUnroll; ++j)
+                    stage(w, my_stage, ns, has_[j], ent_[j], lane, st_spill);
             }
+#pragma unroll
+            for (int j = 0; j < kRelUnroll; ++j)
+                if (pfl_[j] & kInflight)
+                    racy = pgo_[j];
         }
         stage(w, my_stage, ns, c_has, ((u64)x << 32) | (u64)c_t, lane, st_spill);
         if (c_fl & kInflight)
@@ -861,6 +896,8 @@ __global__ void sched_kernel(KParams p)
         }
         if (run)
             __stcs(&p.outv[u], x);
+        if (p.trace && act)
+            p.trace[2ull * u + 1ull] = globaltimer();
         // ---- a warp whose step produced at most kHandMax activations runs
         // them itself next (a chain never leaves the warp); wider output is
         // published to the block's ring / public deque, where it merges with
@@ -1074,12 +1111,29 @@ size_t sched_dyn_smem(u32 smem_entries, u32 warps)
 
 cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bool serve)
 {
-    cudaError_t e = cudaFuncSetAttribute(sched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    // The dynamic shared-memory limit of a kernel is a per-device attribute:
+    // it only ever rises, so that a smaller block shape checked here (a
+    // server, another context) never invalidates a larger one in use.
+    static std::mutex mu;
+    static size_t raised[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return e;
-    e = cudaFuncSetAttribute(sched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-    if (e != cudaSuccess)
-        return e;
+    if (dev < 0 || dev >= 64)
+        return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dyn_smem > raised[dev]) {
+            e = cudaFuncSetAttribute(sched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            if (e != cudaSuccess)
+                return e;
+            e = cudaFuncSetAttribute(sched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            if (e != cudaSuccess)
+                return e;
+            raised[dev] = dyn_smem;
+        }
+    }
     if (serve)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<true>, threads, dyn_smem);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false>, threads, dyn_smem);

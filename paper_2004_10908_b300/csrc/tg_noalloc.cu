@@ -261,6 +261,7 @@ extern "C" int tg_run_noalloc(uint32_t n_nodes, const uint8_t *kinds, const uint
     p.dqc = (QCtr *)(base + kOffDqc);
     p.dq_mask = kNaDequeDepth - 1u;
     p.dq_stride = kNaDequeDepth;
+    p.batch_max = 32;
     p.smem_mask = kNaRing - 1u;
     p.flags = 0;
     p.max_steal = 8;

@@ -150,3 +150,25 @@ def test_submit_and_poll_while_serving(ex):
     for g, t in zip(gs, ts):
         _same(ex.result(t), oracle.run(g, exec_cap=100_000), g.name)
         t.destroy()
+
+
+def test_plain_runs_after_serving_and_beside_other_block_shapes(orc):
+    """A server (narrower blocks) or a second context with another block
+    shape checked in between must leave a context's own launch shape valid."""
+    from paper_2004_10908_b300 import Executor
+    g = _templates(1, seed=8, n_hi=3000)[0]
+    ref = orc.run(g, exec_cap=100_000)
+    with Executor(arena_bytes=256 << 20, warps_per_block=16) as wide, \
+            Executor(arena_bytes=256 << 20, warps_per_block=4) as narrow:
+        hw, hn = wide.graph(g), narrow.graph(g)
+        for _ in range(2):
+            assert wide.run(hw) == 0
+            _same(wide.result(hw), ref, "wide")
+            assert narrow.run(hn) == 0
+            _same(narrow.result(hn), ref, "narrow")
+        wide.serve_start()
+        assert wide.wait(wide.submit(hw)) == 0
+        assert wide.serve_stop() == 0
+        _same(wide.result(hw), ref, "served")
+        assert wide.run(hw) == 0
+        _same(wide.result(hw), ref, "after serving")
