@@ -662,8 +662,10 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
         outdeg[v] = acc;   // reuse as the fill cursor
         acc += (u32)(s.deg & 0xFFFFu);
     }
+    // a static task's edge to a task with no other strong in-edge is marked:
+    // its release needs no join-word update
     for (u32 e = 0; e < m; ++e)
-        he[outdeg[src[e]]++] = dst[e];
+        he[outdeg[src[e]]++] = dst[e] | ((kinds[src[e]] == TG_STATIC && sin[dst[e]] == 1u) ? kSoleBit : 0u);
     for (u32 v = 0, k = 0; v < n; ++v)
         if (sin[v] == 0 && win[v] == 0)
             he[m + k++] = v;

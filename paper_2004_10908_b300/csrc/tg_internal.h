@@ -96,6 +96,8 @@ constexpr u64 kEmpty = 0xFFFFFFFFFFFFFFFFull;
 constexpr u32 kStrongBit = 0x80000000u;   // in a ready entry's low word
 constexpr u32 kInflight = 0x80000000u;    // in NodeSlot::cnt
 constexpr u32 kMaxNodeIndex = 0x7FFFFFFEu;
+constexpr u32 kSoleBit = 0x80000000u;     // in a static task's successor id: the target has
+                                          // strong in-degree 1 (its join word is never used)
 constexpr u32 kChunkShift = 8;            // node ranges are allocated in 256-task chunks
 constexpr u32 kChunk = 1u << kChunkShift;
 

@@ -5,7 +5,9 @@
 // their payloads, dispatches conditions (Algorithm 4: a condition submits
 // successors[r] and touches no join counter) and releases the strong
 // successors of static tasks with 64-bit atomics on their join words
-// (Algorithm 4: decrement, submit at zero).  Ready activations live in
+// (Algorithm 4: decrement, submit at zero); a successor whose only strong
+// in-edge this is needs no counter (the decrement would always reach zero)
+// and is submitted directly.  Ready activations live in
 //   - a per-block ring in shared memory (the worker's local queue, Alg. 5),
 //   - a per-block public deque in global memory that other blocks steal
 //     from (Alg. 6/7: random victims, at most max_steal probes a round),
@@ -665,7 +667,8 @@ __global__ void sched_kernel(KParams p)
             for (int j = 0; j < kRelUnroll; ++j) {
                 v_[j] = j0 + (u32)j < c;
                 ow_[j] = (u32)lane;
-                s_[j] = v_[j] ? c_base + ld_imm<kServe>(&p.edges[succ_off + j0 + (u32)j]) : 0u;
+                const u32 r = v_[j] ? ld_imm<kServe>(&p.edges[succ_off + j0 + (u32)j]) : 0u;
+                s_[j] = v_[j] ? (c_base + (r & ~kSoleBit)) | (r & kSoleBit) : 0u;
             }
         };
         auto fetch_flat = [&](u32 base) {
@@ -685,7 +688,8 @@ __global__ void sched_kernel(KParams p)
                 const u32 ex_o = __shfl_sync(kFull, excl, o);
                 const u32 base_o = __shfl_sync(kFull, c_base, o);
                 ow_[j] = (u32)o;
-                s_[j] = v_[j] ? base_o + ld_imm<kServe>(&p.edges[off_o + (eq - ex_o)]) : 0u;
+                const u32 r = v_[j] ? ld_imm<kServe>(&p.edges[off_o + (eq - ex_o)]) : 0u;
+                s_[j] = v_[j] ? (base_o + (r & ~kSoleBit)) | (r & kSoleBit) : 0u;
             }
         };
         if (per_lane) {
@@ -770,7 +774,7 @@ __global__ void sched_kernel(KParams p)
         if (run && kind != TG_STATIC) {
             int r = cond_index(kind, arg, c_seed, lid, iter, succ_cnt);
             if (r >= 0 && (u32)r < succ_cnt) {
-                c_t = c_base + ld_imm<kServe>(&p.edges[succ_off + (u32)r]);
+                c_t = c_base + (ld_imm<kServe>(&p.edges[succ_off + (u32)r]) & ~kSoleBit);
                 c_has = true;
                 mp++;
                 if (race_check) {
@@ -793,25 +797,32 @@ __global__ void sched_kernel(KParams p)
 #pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j) {
                     v_[j] = v_[j] && run;
-                    old_[j] = v_[j] ? atomicAdd(&p.slots[s_[j]].W, ((u64)x << 32) - 1ull) : 0ull;
+                    // a target with no other strong in-edge is ready at once,
+                    // with this task's output as its input sum
+                    old_[j] = (v_[j] && (s_[j] & kSoleBit) == 0u)
+                                  ? atomicAdd(&p.slots[s_[j]].W, ((u64)x << 32) - 1ull) : 0ull;
                 }
 #pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j) {
+                    const bool sole = (s_[j] & kSoleBit) != 0u;
+                    const u32 t = s_[j] & ~kSoleBit;
                     fl_[j] = 0u;
-                    has_[j] = v_[j] && (u32)old_[j] == 1u;
+                    has_[j] = v_[j] && (sole || (u32)old_[j] == 1u);
                     if (has_[j]) {
                         mp++;
                         if (race_check) {
-                            if (s_[j] == u)
+                            if (t == u)
                                 keep_self = true;
                             else
-                                fl_[j] = atomicOr(&p.slots[s_[j]].cnt, kInflight);
+                                fl_[j] = atomicOr(&p.slots[t].cnt, kInflight);
                         }
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j) {
-                    const u64 ent = ((u64)((u32)(old_[j] >> 32) + x) << 32) | kStrongBit | (u64)s_[j];
+                    const u32 t = s_[j] & ~kSoleBit;
+                    const u64 ent = (s_[j] & kSoleBit) ? (((u64)x << 32) | (u64)t)
+                                                       : (((u64)((u32)(old_[j] >> 32) + x) << 32) | kStrongBit | (u64)t);
                     stage(w, my_stage, ns, has_[j], ent, lane, st_spill);
                     if (fl_[j] & kInflight)
                         racy = gid;
@@ -840,7 +851,8 @@ __global__ void sched_kernel(KParams p)
                 }
 #pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j)
-                    old_[j] = v_[j] ? atomicAdd(&p.slots[s_[j]].W, ((u64)xo_[j] << 32) - 1ull) : 0ull;
+                    old_[j] = (v_[j] && (s_[j] & kSoleBit) == 0u)
+                                  ? atomicAdd(&p.slots[s_[j]].W, ((u64)xo_[j] << 32) - 1ull) : 0ull;
 #pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j)
                     if (pfl_[j] & kInflight)
@@ -848,18 +860,21 @@ __global__ void sched_kernel(KParams p)
 #pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j) {
                     const u32 uo = __shfl_sync(kFull, u, (int)ow_[j]);
+                    const bool sole = (s_[j] & kSoleBit) != 0u;
+                    const u32 t = s_[j] & ~kSoleBit;
                     fl_[j] = 0u;
-                    has_[j] = v_[j] && (u32)old_[j] == 1u;
+                    has_[j] = v_[j] && (sole || (u32)old_[j] == 1u);
                     if (has_[j]) {
                         atomicAdd(&my_push[ow_[j]], 1u);
                         if (race_check) {
-                            if (s_[j] == uo)
+                            if (t == uo)
                                 my_keep[ow_[j]] = 1u;
                             else
-                                fl_[j] = atomicOr(&p.slots[s_[j]].cnt, kInflight);
+                                fl_[j] = atomicOr(&p.slots[t].cnt, kInflight);
                         }
                     }
-                    ent_[j] = ((u64)((u32)(old_[j] >> 32) + xo_[j]) << 32) | kStrongBit | (u64)s_[j];
+                    ent_[j] = sole ? (((u64)xo_[j] << 32) | (u64)t)
+                                   : (((u64)((u32)(old_[j] >> 32) + xo_[j]) << 32) | kStrongBit | (u64)t);
                     pfl_[j] = fl_[j];
                     pgo_[j] = go_[j];
                 }
@@ -887,12 +902,17 @@ __global__ void sched_kernel(KParams p)
         if (racy != kEmpty32)
             atomicCAS(&p.descs[racy].status, 0, TG_ERR_RACE);
 
-        // ---- release own in-flight flags (with the new count and digest)
+        // ---- release own in-flight flags (with the new count and digest).
+        // The fence orders them before the publication of new work; a step
+        // that publishes nothing (it keeps its output in hand) leaves it to
+        // the next step that does.  The server always fences: the host reads
+        // its completion records while it runs.
         if (race_check) {
             if (run)
                 __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt),
                        make_uint2((iter + 1u) | (keep_self ? kInflight : 0u), dg));
-            fence_acq_rel_gpu();
+            if (kServe || ns > kHandMax)
+                fence_acq_rel_gpu();
         }
         if (run)
             __stcs(&p.outv[u], x);

@@ -126,8 +126,10 @@ __global__ void na_pack_kernel(u32 n, u32 m, const u8 *kinds, const u32 *params,
         s.dig = 0;
         slots[v] = s;
         gidv[v >> kChunkShift] = 0;
-        for (u32 e = a; e < b; ++e)
-            edges[e] = succ[e];
+        for (u32 e = a; e < b; ++e) {
+            const u32 t = succ[e];
+            edges[e] = t | ((kind == TG_STATIC && t < n && strong[t] == 1u) ? kSoleBit : 0u);
+        }
         if (strong[v] == 0 && weak[v] == 0) {
             u32 k = atomicAdd((u32 *)&words[W_NSRC], 1u);
             edges[m + k] = v;
