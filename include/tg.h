@@ -245,6 +245,10 @@ typedef struct {
     uint64_t pops_hand;        /* batches a warp kept from its own previous step */
     uint64_t kernel_ns;        /* device time of the last scheduler launch */
     uint32_t worker_blocks, warps_per_block;
+    uint64_t phase_cycles[5];  /* TG_OPT_TRACE only: SM cycles of the steps that executed work,
+                                  split into taking the work, reading the task records, the
+                                  payloads, the releases (with their race checks), and the
+                                  flag release / publication / pending-count settle */
 } tg_stats;
 int tg_ctx_get_stats(tg_ctx *ctx, tg_stats *st);
 int tg_ctx_get_opts(const tg_ctx *ctx, tg_ctx_opts *opts);

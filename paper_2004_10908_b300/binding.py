@@ -57,10 +57,11 @@ class tg_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("tasks", "pops_local", "pops_own", "steal_attempts", "steal_hits", "inject_pops",
                  "spills", "idle_loops", "warp_iters", "pops_hand", "kernel_ns")] + \
-               [("worker_blocks", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32)]
+               [("worker_blocks", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
+                ("phase_cycles", ctypes.c_uint64 * 5)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: (list(getattr(self, k)) if k == "phase_cycles" else getattr(self, k)) for k, _ in self._fields_}
 
 
 _vp = ctypes.c_void_p

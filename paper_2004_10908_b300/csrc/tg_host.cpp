@@ -1351,6 +1351,8 @@ int tg_ctx_get_stats(tg_ctx *c, tg_stats *st)
         st->idle_loops += s[ST_IDLE];
         st->warp_iters += s[ST_ITERS];
         st->pops_hand += s[ST_HAND];
+        for (int i = 0; i < 5; ++i)
+            st->phase_cycles[i] += s[ST_PHASE0 + i];
     }
     if (c->timed) {
         float ms = 0.f;

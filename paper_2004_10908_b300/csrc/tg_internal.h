@@ -88,7 +88,7 @@ struct alignas(128) LaunchCtl {
 
 enum StatIdx {
     ST_TASKS = 0, ST_POP_LOCAL, ST_POP_OWN, ST_STEAL_TRY, ST_STEAL_HIT, ST_INJECT,
-    ST_SPILL, ST_IDLE, ST_ITERS, ST_HAND, ST_COUNT = 16
+    ST_SPILL, ST_IDLE, ST_ITERS, ST_HAND, ST_PHASE0, ST_COUNT = 16   // ST_PHASE0 .. +4: traced cycles
 };
 
 constexpr u32 kEmpty32 = 0xFFFFFFFFu;

@@ -333,6 +333,7 @@ __global__ void sched_kernel(KParams p)
     __shared__ u32 s_keep[32 * 32];
     __shared__ u64 s_stats[ST_COUNT];
     __shared__ int s_thief, s_stop, s_hungry;
+    __shared__ u64 s_tmark[32];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -393,9 +394,21 @@ __global__ void sched_kernel(KParams p)
     u32 c_gid = kEmpty32, c_seed = 0, c_cap = 0, c_age = 0, c_base = 0;
     i32 c_status = 0;
 
+    // traced launches: cycles per phase of a step, marked by lane 0 (the
+    // previous mark of each warp lives in shared memory)
+    const bool traced = p.trace != nullptr;
+    auto mark = [&](int phase) {
+        if (traced && lane == 0) {
+            const u64 t = clock64();
+            if (phase >= 0)
+                atomicAdd(&s_stats[ST_PHASE0 + phase], t - s_tmark[warp]);
+            s_tmark[warp] = t;
+        }
+    };
     for (;;) {
         u64 e = kEmpty;
         int k = 0;
+        mark(-1);
         if (nh) {
             e = hand;
             k = nh;
@@ -604,6 +617,7 @@ __global__ void sched_kernel(KParams p)
             }
         }
         st_iters++;
+        mark(0);
         if (lane == 0 && *(volatile int *)&s_hungry != 0 && atomicExch(&s_hungry, 0) == 1)
             atomicSub(&p.ctl->hungry, 1u);
 
@@ -659,6 +673,10 @@ __global__ void sched_kernel(KParams p)
         const u32 c = (act && kind == TG_STATIC) ? succ_cnt : 0u;
         const u32 maxc = __reduce_max_sync(kFull, c);
         const bool per_lane = maxc <= kPerLaneMax;
+        if (traced) {
+            asm volatile("" ::"r"(maxc), "r"(iter), "r"(lid), "r"(c_seed));
+            mark(1);
+        }
         u32 s_[kRelUnroll], ow_[kRelUnroll];
         bool v_[kRelUnroll];
         u32 total = 0, excl = 0;
@@ -721,6 +739,10 @@ __global__ void sched_kernel(KParams p)
         // ---- payload
         const u32 x = act ? task_payload(lid, iter, insum, rounds) : 0u;
         const u32 dg = mix32(stt.y ^ x);
+        if (traced) {
+            asm volatile("" ::"r"(dg));
+            mark(2);
+        }
 
         const bool run = act && c_status == 0;
         const u32 U = run ? (kind == TG_STATIC ? succ_cnt : 1u) : 0u;
@@ -892,6 +914,10 @@ __global__ void sched_kernel(KParams p)
         stage(w, my_stage, ns, c_has, ((u64)x << 32) | (u64)c_t, lane, st_spill);
         if (c_fl & kInflight)
             racy = gid;
+        if (traced) {
+            asm volatile("" ::"r"(racy), "r"(ns), "r"(mp));
+            mark(3);
+        }
         __syncwarp();
         if (!per_lane) {
             mp += my_push[lane];
@@ -970,6 +996,7 @@ __global__ void sched_kernel(KParams p)
                 }
             }
         }
+        mark(4);
         if (w.err) {
             if (lane == 0)
                 atomicCAS(&p.ctl->abort_code, 0, TG_ERR_INTERNAL);
