@@ -157,6 +157,13 @@ def algorithmic_bytes(g):
     return 44 * g.n + 20 * g.m
 
 
+def critical_path_tasks(g):
+    """Tasks on the longest path of the layered or wavefront DAG."""
+    if "levels" in g.meta:
+        return int(g.meta["levels"])
+    return 2 * int(g.meta["side"]) - 1
+
+
 def headline(ex, graphs, args, torch, B):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = ex.stream
@@ -362,6 +369,15 @@ def run_b300(args):
     for g in graphs:
         ns, _ = ex.bench_payload(g.n, int(g.params[0] & 0xFFFF))
         pay_ns += ns
+    # the dependency floor: the payloads along each graph's longest path run
+    # back to back by one thread, with no scheduling at all
+    crit = {}
+    for g in graphs:
+        hops = critical_path_tasks(g)
+        floor_ns = min(ex.bench_chain(hops, int(g.params[0] & 0xFFFF))[0] for _ in range(3))
+        crit[g.name] = {"path_tasks": hops, "floor_ms": floor_ns / 1e6, "sched_ms": per_graph[g.name] / 1e6,
+                        "frac": floor_ns / per_graph[g.name],
+                        "overhead_us_per_hop": (per_graph[g.name] - floor_ns) / 1e3 / hops}
     atom_ns = ex.bench_atomics(1 << 26, 1 << 24)
     atom_ceiling = (1 << 26) / (atom_ns * 1e-9)
     atomics_per_launch = sum(g.m + 2 * g.n for g in graphs)   # releases + in-flight flag + re-arm
@@ -388,6 +404,7 @@ def run_b300(args):
         "atomics": {"ceiling_per_s": atom_ceiling, "achieved_per_s": atomics_per_launch / (sched_ns * 1e-9),
                     "frac": atomics_per_launch / (sched_ns * 1e-9) / atom_ceiling},
         "per_graph_sched_ms": {k: v / 1e6 for k, v in per_graph.items()},
+        "critical_path": crit,
         "scheduler_stats": {k: stats[k] for k in ("steal_attempts", "steal_hits", "spills", "warp_iters",
                                                   "pops_hand", "pops_local")},
         "gpu_launches": 3 * len(graphs) * args.steps,

@@ -266,9 +266,14 @@ int tg_ctx_set_launch(tg_ctx *ctx, const tg_ctx_opts *launch);
  *    XOR of all outputs (to compare with the oracle's payload).
  *  tg_bench_atomics: `count` returning 64-bit atomicAdd at distinct
  *    pseudo-random addresses over `footprint_words` 8-byte words of arena
- *    scratch; *ns = device time. */
+ *    scratch; *ns = device time.
+ *  tg_bench_chain: the dependency floor of a graph whose longest path has
+ *    `hops` tasks of `rounds` rounds: one thread runs `hops` payloads in a
+ *    row, each taking the previous output as its input sum (no scheduling);
+ *    *ns = device time, *last = the final output. */
 int tg_bench_payload(tg_ctx *ctx, uint64_t count, uint32_t rounds, uint64_t *ns, uint32_t *checksum);
 int tg_bench_atomics(tg_ctx *ctx, uint64_t count, uint64_t footprint_words, uint64_t *ns);
+int tg_bench_chain(tg_ctx *ctx, uint32_t hops, uint32_t rounds, uint64_t *ns, uint32_t *last);
 
 /* Run one graph without allocating anything (the paper has no counterpart:
  * this exists for callers that cannot allocate device memory, e.g. code

@@ -99,6 +99,7 @@ SIGNATURES = {
                                          ctypes.POINTER(_u64)]),
     "tg_bench_payload": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "tg_bench_atomics": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(_u64)]),
+    "tg_bench_chain": (ctypes.c_int, [_vp, _u32, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "tg_run_noalloc": (ctypes.c_int, [_u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]),
     "tg_trace_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "tg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -297,6 +298,14 @@ def tg_bench_payload(ctx, count, rounds):
     cs = _u32(0)
     _check(load().tg_bench_payload(_vp(ctx), count, rounds, ctypes.byref(ns), ctypes.byref(cs)), "tg_bench_payload")
     return ns.value, cs.value
+
+
+def tg_bench_chain(ctx, hops, rounds):
+    """Returns (device ns, final output) of `hops` dependent payloads."""
+    ns = _u64(0)
+    last = _u32(0)
+    _check(load().tg_bench_chain(_vp(ctx), hops, rounds, ctypes.byref(ns), ctypes.byref(last)), "tg_bench_chain")
+    return ns.value, last.value
 
 
 def tg_bench_atomics(ctx, count, footprint_words):

@@ -1402,6 +1402,25 @@ int tg_bench_atomics(tg_ctx *c, uint64_t count, uint64_t footprint_words, uint64
     return TG_OK;
 }
 
+int tg_bench_chain(tg_ctx *c, uint32_t hops, uint32_t rounds, uint64_t *ns, uint32_t *last)
+{
+    if (!c || !ns || rounds > 0xFFFFu)
+        return TG_ERR_INVALID;
+    TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    TG_CUDA(launch_bench_chain(hops, rounds, c->scratch, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    u32 out = 0;
+    TG_CUDA(cudaMemcpyAsync(&out, c->scratch, 4, cudaMemcpyDeviceToHost, c->stream));
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    TG_CUDA(cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1));
+    *ns = (u64)((double)ms * 1e6);
+    if (last)
+        *last = out;
+    c->timed = false;
+    return TG_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -152,5 +152,6 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
 size_t sched_dyn_smem(u32 smem_entries, u32 warps);
 cudaError_t launch_bench_payload(u64 count, u32 rounds, u32 *checksum, cudaStream_t st);
 cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink, cudaStream_t st);
+cudaError_t launch_bench_chain(u32 hops, u32 rounds, u32 *last, cudaStream_t st);
 
 }  // namespace tg

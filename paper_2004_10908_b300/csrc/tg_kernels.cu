@@ -1135,6 +1135,15 @@ __global__ void bench_payload_kernel(u64 count, u32 rounds, u32 *checksum)
         atomicXor(checksum, acc);
 }
 
+// The compute along a path of `hops` dependent tasks, with nothing else.
+__global__ void bench_chain_kernel(u32 hops, u32 rounds, u32 *last)
+{
+    u32 x = 0;
+    for (u32 h = 0; h < hops; ++h)
+        x = task_payload(h, 0u, x, rounds);
+    *last = x;
+}
+
 // `count` returning 64-bit atomicAdd at pseudo-random words of a footprint.
 __global__ void bench_atomics_kernel(u64 *words, u64 footprint, u64 count, u64 *sink)
 {
@@ -1238,6 +1247,12 @@ cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     bench_atomics_kernel<<<sms * 8, 256, 0, st>>>(words, footprint, count, sink);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bench_chain(u32 hops, u32 rounds, u32 *last, cudaStream_t st)
+{
+    bench_chain_kernel<<<1, 1, 0, st>>>(hops, rounds, last);
     return cudaGetLastError();
 }
 

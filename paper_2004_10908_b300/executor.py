@@ -152,6 +152,9 @@ class Executor:
     def bench_atomics(self, count, footprint_words):
         return B.tg_bench_atomics(self.ctx, count, footprint_words)
 
+    def bench_chain(self, hops, rounds):
+        return B.tg_bench_chain(self.ctx, hops, rounds)
+
     def close(self):
         if self.ctx:
             B.tg_ctx_destroy(self.ctx)

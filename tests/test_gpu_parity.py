@@ -195,3 +195,14 @@ def test_payload_kernel_matches_oracle_payload(ex):
         ns, cs = ex.bench_payload(n, R)
         ref = oracle.payload_many(np.arange(n), np.zeros(n), np.zeros(n), np.full(n, R))
         assert cs == int(np.bitwise_xor.reduce(ref)), R
+
+
+def test_chain_floor_kernel_matches_oracle_payload_chain(ex):
+    """The dependency-floor kernel computes the payloads of a path: output
+    of hop h feeds the input sum of hop h + 1."""
+    for hops, R in ((1, 0), (37, 5), (300, 16)):
+        ns, last = ex.bench_chain(hops, R)
+        x = 0
+        for h in range(hops):
+            x = oracle.payload(h, 0, x, R)
+        assert last == x, (hops, R)
