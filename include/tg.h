@@ -97,7 +97,11 @@ typedef struct {
     int32_t batch_max;         /* activations a warp takes per step, 1..32 [32] */
     int32_t local_keep;        /* ready activations a block keeps in shared memory before the
                                   rest goes to its stealable deque, <= smem_ring [32] */
-    int32_t reserved;
+    int32_t thief_mode;        /* 0: at most max_thieves blocks steal at once; 1: adaptive
+                                  (Alg. 3/6): while a block is active at least one block
+                                  steals, a failed thief other than the last one parks, and
+                                  the last thief to find work wakes one parked block.  The
+                                  resident server always uses 0. [0] */
     uint64_t time_limit_ns;    /* device time limit per launch [10 s] */
     uint64_t exec_cap;         /* executions per graph before TG_ERR_EXEC_LIMIT [2^31] */
     uint64_t mem_budget_bytes; /* admission budget for graph memory [the node/edge pools] */
@@ -249,6 +253,10 @@ typedef struct {
                                   split into taking the work, reading the task records, the
                                   payloads, the releases (with their race checks), and the
                                   flag release / publication / pending-count settle */
+    uint64_t parks;            /* thief_mode 1: times a failed thief parked its block */
+    uint64_t peak_thieves;     /* most blocks stealing at the same time (thief_mode 1) */
+    uint64_t failed_rounds;    /* steal rounds (own deque, advertised victims, injection
+                                  queue) that found nothing: the polling a thief policy wastes */
 } tg_stats;
 int tg_ctx_get_stats(tg_ctx *ctx, tg_stats *st);
 int tg_ctx_get_opts(const tg_ctx *ctx, tg_ctx_opts *opts);

@@ -40,7 +40,7 @@ class tg_ctx_opts(ctypes.Structure):
                 ("max_steal", ctypes.c_int32), ("smem_ring", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("idle_sleep_ns", ctypes.c_uint32),
                 ("max_thieves", ctypes.c_int32), ("batch_max", ctypes.c_int32),
-                ("local_keep", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("local_keep", ctypes.c_int32), ("thief_mode", ctypes.c_int32),
                 ("time_limit_ns", ctypes.c_uint64), ("exec_cap", ctypes.c_uint64),
                 ("mem_budget_bytes", ctypes.c_uint64), ("max_nodes", ctypes.c_uint64),
                 ("max_edges", ctypes.c_uint64)]
@@ -58,7 +58,8 @@ class tg_stats(ctypes.Structure):
                 ("tasks", "pops_local", "pops_own", "steal_attempts", "steal_hits", "inject_pops",
                  "spills", "idle_loops", "warp_iters", "pops_hand", "kernel_ns")] + \
                [("worker_blocks", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
-                ("phase_cycles", ctypes.c_uint64 * 5)]
+                ("phase_cycles", ctypes.c_uint64 * 5), ("parks", ctypes.c_uint64),
+                ("peak_thieves", ctypes.c_uint64), ("failed_rounds", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k == "phase_cycles" else getattr(self, k)) for k, _ in self._fields_}

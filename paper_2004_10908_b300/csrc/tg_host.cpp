@@ -26,7 +26,7 @@ constexpr u32 kSubRing = 1u << 16;  // server-mode submission / completion ring 
 // keeps the one it was captured with), within what the context allocated.
 struct Geometry {
     int blocks = 0, threads = 0;
-    u32 ring = 0, depth = 0, policy = 0, max_steal = 0, thieves = 0, idle_ns = 0, batch = 32, keep = 0;
+    u32 ring = 0, depth = 0, policy = 0, max_steal = 0, thieves = 0, idle_ns = 0, batch = 32, keep = 0, tmode = 0;
 };
 
 u64 now_ns()
@@ -227,6 +227,7 @@ KParams base_params(tg_ctx *c, const Geometry &g)
     p.max_thieves = g.thieves;
     p.batch_max = g.batch;
     p.local_keep = g.keep;
+    p.thief_mode = g.tmode;
     p.thief_slots = c->thief_slots;
     p.time_limit_ns = c->opts.time_limit_ns;
     p.cancel = c->d_cancel;
@@ -293,7 +294,7 @@ int resolve_geometry(const tg_ctx *c, const tg_ctx_opts &o, Geometry &g)
     if (warps > 32 || !is_pow2(ring) || ring < 64 || ring > 8192 || !is_pow2(depth) || depth < 64 ||
         depth > c->dq_cap || o.steal_policy < 0 || o.steal_policy > 1 || o.max_thieves > 1024 ||
         o.max_steal < 0 || o.worker_blocks < 0 || o.batch_max < 0 || o.batch_max > 32 || o.local_keep < 0 ||
-        (u32)o.local_keep > ring)
+        (u32)o.local_keep > ring || o.thief_mode < 0 || o.thief_mode > 1)
         return TG_ERR_INVALID;
     int per_sm = 0;
     if (sched_occupancy(warps * 32, sched_dyn_smem(ring, (u32)warps), &per_sm) != cudaSuccess || per_sm <= 0)
@@ -311,6 +312,7 @@ int resolve_geometry(const tg_ctx *c, const tg_ctx_opts &o, Geometry &g)
     // a short shared-memory backlog: ready work beyond it goes to the block's
     // public deque where idle warps of other blocks can take it
     g.keep = std::min<u32>(o.local_keep > 0 ? (u32)o.local_keep : 32u, ring);
+    g.tmode = (u32)o.thief_mode;
     return TG_OK;
 }
 
@@ -326,6 +328,7 @@ void geometry_to_opts(const Geometry &g, tg_ctx_opts &o)
     o.idle_sleep_ns = g.idle_ns;
     o.batch_max = (int32_t)g.batch;
     o.local_keep = (int32_t)g.keep;
+    o.thief_mode = (int32_t)g.tmode;
 }
 
 }  // namespace
@@ -1204,9 +1207,10 @@ int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache
                     continue;
                 tg_ctx_opts o{};
                 unsigned long long t = 0;
-                if (std::sscanf(tab + 1, "%d %d %d %d %d %d %d %u %d %d %llu", &o.worker_blocks,
+                if (std::sscanf(tab + 1, "%d %d %d %d %d %d %d %u %d %d %d %llu", &o.worker_blocks,
                                 &o.warps_per_block, &o.deque_depth, &o.steal_policy, &o.max_steal, &o.max_thieves,
-                                &o.smem_ring, &o.idle_sleep_ns, &o.batch_max, &o.local_keep, &t) == 11) {
+                                &o.smem_ring, &o.idle_sleep_ns, &o.batch_max, &o.local_keep, &o.thief_mode,
+                                &t) == 12) {
                     Geometry g;
                     if (resolve_geometry(c, o, g) == TG_OK) {
                         best = o;
@@ -1255,6 +1259,7 @@ int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache
         const int thief_c[] = {8, 16, 64};
         const int batch_c[] = {8, 16, 32};
         const int keep_c[] = {16, 32, 128, 512};
+        const int tmode_c[] = {0, 1};
         auto try_knob = [&](auto setter, const int *vals, int nv) -> int {
             for (int i = 0; i < nv; ++i) {
                 tg_ctx_opts o = best;
@@ -1286,14 +1291,15 @@ int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache
             (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.max_steal = v; }, steal_c, 3)) != TG_OK ||
             (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.max_thieves = v; }, thief_c, 3)) != TG_OK ||
             (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.batch_max = v; }, batch_c, 3)) != TG_OK ||
-            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.local_keep = v; }, keep_c, 4)) != TG_OK)
+            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.local_keep = v; }, keep_c, 4)) != TG_OK ||
+            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.thief_mode = v; }, tmode_c, 2)) != TG_OK)
             return rc2;
         if (cache_path) {
             if (FILE *f = std::fopen(cache_path, "a")) {
-                std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %d %d %llu\n", key.c_str(), best.worker_blocks,
+                std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %d %d %d %llu\n", key.c_str(), best.worker_blocks,
                              best.warps_per_block, best.deque_depth, best.steal_policy, best.max_steal,
                              best.max_thieves, best.smem_ring, best.idle_sleep_ns, best.batch_max, best.local_keep,
-                             (unsigned long long)best_t);
+                             best.thief_mode, (unsigned long long)best_t);
                 std::fclose(f);
             }
         }
@@ -1353,6 +1359,9 @@ int tg_ctx_get_stats(tg_ctx *c, tg_stats *st)
         st->pops_hand += s[ST_HAND];
         for (int i = 0; i < 5; ++i)
             st->phase_cycles[i] += s[ST_PHASE0 + i];
+        st->parks += s[ST_PARK];
+        st->failed_rounds += s[ST_FAILED_ROUND];
+        st->peak_thieves = std::max<uint64_t>(st->peak_thieves, s[ST_PEAK_THIEVES]);
     }
     if (c->timed) {
         float ms = 0.f;

@@ -84,11 +84,18 @@ struct alignas(128) LaunchCtl {
     u32 pad5[31];
     u32 stop;        // server mode: set by the host (copy engine) to end the server
     u32 pad6[31];
+    u32 actives;     // thief_mode 1: blocks with a warp executing work
+    u32 pad7[31];
+    u32 thieves;     // thief_mode 1: blocks stealing
+    u32 pad8[31];
+    u32 wake;        // thief_mode 1: wake tickets for parked blocks
+    u32 pad9[31];
 };
 
 enum StatIdx {
     ST_TASKS = 0, ST_POP_LOCAL, ST_POP_OWN, ST_STEAL_TRY, ST_STEAL_HIT, ST_INJECT,
-    ST_SPILL, ST_IDLE, ST_ITERS, ST_HAND, ST_PHASE0, ST_COUNT = 16   // ST_PHASE0 .. +4: traced cycles
+    ST_SPILL, ST_IDLE, ST_ITERS, ST_HAND, ST_PHASE0,   // ST_PHASE0 .. +4: traced cycles
+    ST_PARK = ST_PHASE0 + 5, ST_PEAK_THIEVES, ST_FAILED_ROUND, ST_COUNT = 24
 };
 
 constexpr u32 kEmpty32 = 0xFFFFFFFFu;
@@ -130,7 +137,7 @@ struct KParams {
     u32 dq_stride;         // entries allocated per block deque (>= dq_mask + 1)
     u32 batch_max;         // activations a warp takes per step (1..32)
     u32 local_keep;        // shared-memory ring size above which new work goes public (0 = default)
-    u32 pad4;
+    u32 thief_mode;        // 0 capped thief slots, 1 adaptive (parks and wake tickets)
     u32 *thief_slots;      // max_thieves words, each on its own 128-byte line
     u64 time_limit_ns;
     u64 *trace;            // TG_OPT_TRACE: per task {start ns, publish ns} (may be null)

@@ -333,6 +333,7 @@ __global__ void sched_kernel(KParams p)
     __shared__ u32 s_keep[32 * 32];
     __shared__ u64 s_stats[ST_COUNT];
     __shared__ int s_thief, s_stop, s_hungry;
+    __shared__ u32 s_busy, s_peak;
     __shared__ u64 s_tmark[32];
 
     const int lane = threadIdx.x & 31;
@@ -348,6 +349,8 @@ __global__ void sched_kernel(KParams p)
         s_thief = 0;
         s_stop = 0;
         s_hungry = 0;
+        s_busy = 0;
+        s_peak = 0;
     }
     __syncthreads();
 
@@ -377,7 +380,11 @@ __global__ void sched_kernel(KParams p)
     u64 *my_stage = s_ring + ring_n + (size_t)warp * kStage;
 
     u64 st_tasks = 0, st_local = 0, st_own = 0, st_try = 0, st_hit = 0, st_inj = 0, st_spill = 0,
-        st_idle = 0, st_iters = 0, st_hand = 0;
+        st_idle = 0, st_iters = 0, st_hand = 0, st_park = 0, st_fail = 0;
+    // adaptive thieves (Alg. 3/6 invariant): a block is active while one of
+    // its warps executes; blocks are the workers whose counts are kept
+    const bool adaptive = !kServe && p.thief_mode == 1u;
+    bool busy_w = false;
     u32 rng = mix32(blockIdx.x * 0x9E3779B9U + (u32)warp * 0x85EBCA6BU + 1u);
     bool pend = false;      // a pending-count update whose result is not examined yet
     u64 pend_old = 0, pend_delta = 0;
@@ -420,6 +427,11 @@ __global__ void sched_kernel(KParams p)
                 st_local++;
             } else {
                 settle_finish<kServe>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+                if (adaptive && busy_w) {
+                    busy_w = false;
+                    if (lane == 0 && atomicSub(&s_busy, 1u) == 1u)
+                        atomicSub(&p.ctl->actives, 1u);
+                }
                 // ---- idle.  One warp per block at a time is the block's thief
                 // (Alg. 6/7), and at most max_thieves blocks steal at once; only
                 // thieves poll launch-wide state, the other idle warps wait on
@@ -429,7 +441,10 @@ __global__ void sched_kernel(KParams p)
                 int am = 0;
                 if (lane == 0) {
                     am = atomicCAS(&s_thief, 0, 1) == 0;
-                    if (am && atomicCAS(&p.thief_slots[my_slot * 32u], 0u, 1u) != 0u) {
+                    if (am && adaptive) {
+                        const u32 t = atomicAdd(&p.ctl->thieves, 1u) + 1u;
+                        atomicMax(&s_peak, t);
+                    } else if (am && atomicCAS(&p.thief_slots[my_slot * 32u], 0u, 1u) != 0u) {
                         *(volatile int *)&s_thief = 0;
                         am = 2;
                     }
@@ -578,6 +593,7 @@ __global__ void sched_kernel(KParams p)
                 if (k == 0) {
                     // stop when every graph is done, on abort, timeout or cancel
                     st_idle++;
+                    st_fail++;
                     int stop = 0;
                     if (lane == 0) {
                         const bool done = kServe ? (vld32(&p.ctl->stop) != 0u) : (vld32(&p.ctl->graphs_left) == 0u);
@@ -598,7 +614,46 @@ __global__ void sched_kernel(KParams p)
                             *(volatile int *)&s_stop = 1;
                         else if (atomicExch(&s_hungry, 1) == 0)
                             atomicAdd(&p.ctl->hungry, 1u);
-                        vst32(&p.thief_slots[my_slot * 32u], 0u);
+                    }
+                    if (adaptive) {
+                        // the last thief keeps stealing while a block is active or
+                        // a deque advertises work; any other failed thief parks
+                        // its block until a wake ticket (or the end) arrives
+                        const u32 nwa = (p.nblocks + 31u) >> 5;
+                        const int any = __ballot_sync(kFull, (u32)lane < nwa && vld32(&p.ctl->avail[lane]) != 0u) != 0;
+                        if (lane == 0) {
+                            const bool last = atomicSub(&p.ctl->thieves, 1u) == 1u;
+                            if (!stop && !(last && (any || vld32(&p.ctl->actives) != 0u))) {
+                                st_park++;
+                                u32 nap = 256, naps = 0;
+                                for (;;) {
+                                    __nanosleep(nap);
+                                    nap = min(nap * 2u, 4096u);
+                                    ++naps;
+                                    if (vld32(&p.ctl->graphs_left) == 0u || vldi(&p.ctl->abort_code) != 0) {
+                                        stop = 1;
+                                    } else if (globaltimer() > deadline) {
+                                        atomicCAS(&p.ctl->abort_code, 0, TG_ERR_TIMEOUT);
+                                        stop = 1;
+                                    } else if (p.cancel && (naps & 15u) == 0u && *p.cancel != 0u) {
+                                        atomicCAS(&p.ctl->abort_code, 0, TG_ERR_CANCELLED);
+                                        stop = 1;
+                                    }
+                                    if (stop) {
+                                        *(volatile int *)&s_stop = 1;
+                                        break;
+                                    }
+                                    const u32 tk = vld32(&p.ctl->wake);
+                                    if (tk != 0u && atomicCAS(&p.ctl->wake, tk, tk - 1u) == tk)
+                                        break;
+                                }
+                                backoff = 256;
+                            }
+                        }
+                    }
+                    if (lane == 0) {
+                        if (!adaptive)
+                            vst32(&p.thief_slots[my_slot * 32u], 0u);
                         __threadfence_block();
                         *(volatile int *)&s_thief = 0;
                     }
@@ -610,7 +665,14 @@ __global__ void sched_kernel(KParams p)
                     continue;
                 }
                 if (lane == 0) {
-                    vst32(&p.thief_slots[my_slot * 32u], 0u);
+                    if (adaptive) {
+                        // the last thief to become active wakes a parked block
+                        // to take over its role
+                        if (atomicSub(&p.ctl->thieves, 1u) == 1u)
+                            atomicAdd(&p.ctl->wake, 1u);
+                    } else {
+                        vst32(&p.thief_slots[my_slot * 32u], 0u);
+                    }
                     *(volatile int *)&s_thief = 0;
                 }
                 backoff = 256;
@@ -618,6 +680,11 @@ __global__ void sched_kernel(KParams p)
         }
         st_iters++;
         mark(0);
+        if (adaptive && !busy_w) {
+            busy_w = true;
+            if (lane == 0 && atomicAdd(&s_busy, 1u) == 0u)
+                atomicAdd(&p.ctl->actives, 1u);
+        }
         if (lane == 0 && *(volatile int *)&s_hungry != 0 && atomicExch(&s_hungry, 0) == 1)
             atomicSub(&p.ctl->hungry, 1u);
 
@@ -1029,9 +1096,14 @@ __global__ void sched_kernel(KParams p)
         atomicAdd(&s_stats[ST_IDLE], st_idle);
         atomicAdd(&s_stats[ST_ITERS], st_iters);
         atomicAdd(&s_stats[ST_HAND], st_hand);
+        atomicAdd(&s_stats[ST_PARK], st_park);
+        atomicAdd(&s_stats[ST_FAILED_ROUND], st_fail);
     }
     // tasks are counted per lane
     atomicAdd(&s_stats[ST_TASKS], st_tasks);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_stats[ST_PEAK_THIEVES] = s_peak;
     __syncthreads();
     if (threadIdx.x < ST_COUNT)
         p.stats[(size_t)blockIdx.x * ST_COUNT + threadIdx.x] = s_stats[threadIdx.x];
@@ -1080,6 +1152,9 @@ __global__ void rearm_kernel(KParams p)
             p.ctl->graphs_left = p.n_graphs;
             p.ctl->abort_code = 0;
             p.ctl->hungry = 0u;
+            p.ctl->actives = 0u;
+            p.ctl->thieves = 0u;
+            p.ctl->wake = 0u;
             p.ctl->inj.head = 0u;
             p.ctl->inj.tail = p.total_sources;
             if (p.cancel)

@@ -206,3 +206,34 @@ def test_chain_floor_kernel_matches_oracle_payload_chain(ex):
         for h in range(hops):
             x = oracle.payload(h, 0, x, R)
         assert last == x, (hops, R)
+
+
+def test_adaptive_thieves_parity_and_fewer_wasted_steals():
+    """Adaptive thief mode (Alg. 3/6): same results as the oracle on DAGs,
+    loops, branches and racy-free tiny graphs; on a chain (one task ready at
+    a time) it wastes far fewer steal rounds than a fixed cap of 16 thieves,
+    because all but the last failed thief park."""
+    from paper_2004_10908_b300 import Executor
+    from workloads.graphs import STATIC, from_lists, pack_param
+    graphs = [w.config1(levels=6, width=40, trip=3, rounds=16), w.do_while(200, 4),
+              w.config2a(seed=5, levels=30, width=300, rounds=8),
+              w.config3(seed=3, n_cond=60, body_levels=4, body_width=6, rounds=8, trip_max=6)] + \
+             [w.nested_loops(s) for s in range(6)]
+    with Executor(arena_bytes=1 << 30, thief_mode=1) as ex:
+        assert ex.opts()["thief_mode"] == 1
+        for g in graphs:
+            dev, ref = run_both(ex, g)
+            assert_same(dev, ref, g.name)
+    n = 3000
+    chain = from_lists("chain", [STATIC] * n, [pack_param(0)] * n, [(i, i + 1) for i in range(n - 1)])
+    wasted = {}
+    for mode in (0, 1):
+        with Executor(arena_bytes=1 << 28, thief_mode=mode) as ex:
+            h = ex.graph(chain)
+            assert ex.run(h) == 0
+            s = ex.stats()
+            wasted[mode] = s["failed_rounds"]
+            if mode == 1:
+                assert s["parks"] > 0
+                assert 1 <= s["peak_thieves"] <= s["worker_blocks"]
+    assert wasted[1] * 4 < wasted[0], wasted
