@@ -229,6 +229,30 @@ def e2e(ex, graphs, reps):
     return statistics.mean(ms), h2d, d2h
 
 
+def thief_policies(Executor):
+    """Fixed cap of 16 thieves vs the adaptive invariant (Alg. 3/6) on the
+    plain single graph (config 1) and the two large DAGs: scheduler time and
+    the polling each wastes (steal rounds that found nothing)."""
+    graphs = [w.config1(), w.config2a(), w.config2b()]
+    out = {}
+    for mode in (0, 1):
+        with Executor(arena_bytes=4 << 30, thief_mode=mode) as ex:
+            for g in graphs:
+                h = ex.graph(g)
+                rows = []
+                for _ in range(3):
+                    assert ex.run(h) == 0
+                    s = ex.stats()
+                    rows.append((s["kernel_ns"], s["failed_rounds"], s["parks"], s["peak_thieves"]))
+                h.destroy()
+                rows.sort()
+                ns, failed, parks, peak = rows[1]
+                out.setdefault(g.name, {})["adaptive" if mode else "capped16"] = {
+                    "sched_ms": ns / 1e6, "failed_rounds": failed, "failed_rounds_per_ms": failed / (ns / 1e6),
+                    "parks": parks, "peak_thieves": peak}
+    return out
+
+
 def batched(Executor, torch):
     """4,096 graphs in one autotuned, CUDA-graph-captured launch vs one launch each."""
     t0 = time.time()
@@ -410,6 +434,8 @@ def run_b300(args):
         "gpu_launches": 3 * len(graphs) * args.steps,
         "clocks": clocks,
     }
+    if not SMALL:
+        line["thief_policies"] = thief_policies(Executor)
     if not args.skip_batched and not SMALL:
         line["batched"] = batched(Executor, torch)
     if not args.skip_serving and not SMALL:
