@@ -253,6 +253,44 @@ def thief_policies(Executor):
     return out
 
 
+def capturer_baseline(Executor, torch, B):
+    """Algorithm 1's form (one kernel per task in a CUDA graph over
+    round-robin streams) against the persistent scheduler on static DAGs:
+    the plain single graph's body (10 x 100, in-degree 1-4, 64 rounds) and a
+    wider one (20 x 1,000, in-degree 1-8, 16 rounds).  Whole runs (re-arm
+    included) on the device clock."""
+    out = []
+    for g in (w.config2a(seed=0, levels=10, width=100, d_lo=1, d_hi=4, rounds=64),
+              w.config2a(seed=1, levels=20, width=1000, d_lo=1, d_hi=8, rounds=16)):
+        with Executor(arena_bytes=1 << 30) as ex:
+            h = ex.graph(g)
+            ref = None
+            ts = []
+            for _ in range(6):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(ex.stream)
+                st, t = B.tg_submit(ex.ctx, h.handle)
+                e1.record(ex.stream)
+                assert st == 0 and ex.wait(t) == 0
+                ts.append(e0.elapsed_time(e1))
+            ref = ex.result(h)
+            row = {"graph": f"layered {g.meta['levels']} x {g.meta['width']}, R={int(g.params[0] & 0xFFFF)}",
+                   "tasks": g.n, "persistent_ms": statistics.median(ts[1:]), "cuda_graph_ms": {}}
+            for k in (1, 4, 32):
+                t0 = time.perf_counter()
+                st, _ = ex.capture_run(h, k)
+                build_s = time.perf_counter() - t0
+                assert st == 0
+                ns = sorted(ex.capture_run(h, k)[1] for _ in range(5))[2]
+                got = ex.result(h)
+                assert all((np.asarray(a) == np.asarray(b)).all() for a, b in zip(got[:3], ref[:3]))
+                row["cuda_graph_ms"][str(k)] = {"replay_ms": ns / 1e6, "build_s": build_s}
+            h.destroy()
+        out.append(row)
+    return out
+
+
 def batched(Executor, torch):
     """4,096 graphs in one autotuned, CUDA-graph-captured launch vs one launch each."""
     t0 = time.time()
@@ -436,6 +474,7 @@ def run_b300(args):
     }
     if not SMALL:
         line["thief_policies"] = thief_policies(Executor)
+        line["capturer_baseline"] = capturer_baseline(Executor, torch, B)
     if not args.skip_batched and not SMALL:
         line["batched"] = batched(Executor, torch)
     if not args.skip_serving and not SMALL:

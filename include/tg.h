@@ -283,6 +283,32 @@ int tg_bench_payload(tg_ctx *ctx, uint64_t count, uint32_t rounds, uint64_t *ns,
 int tg_bench_atomics(tg_ctx *ctx, uint64_t count, uint64_t footprint_words, uint64_t *ns);
 int tg_bench_chain(tg_ctx *ctx, uint32_t hops, uint32_t rounds, uint64_t *ns, uint32_t *last);
 
+/* Capturer baseline (Algorithm 1): a static DAG as one kernel per task,
+ * captured into a CUDA graph over round-robin streams.
+ *  tg_levelize: host only.  level[v] = 0 for a task without in-edges, else
+ *    1 + the largest level of its predecessors; index[v] = the task's
+ *    position among the tasks of its level taken in ascending id.
+ *    *n_levels = levels.  TG_ERR_INVALID for a bad index or a cycle.
+ *  tg_stream_plan: host only.  stream[v] = index[v] mod max_streams
+ *    (1..32); *n_events = tasks that record an event because a successor
+ *    sits on another stream; *n_waits = distinct (predecessor, task) pairs
+ *    on different streams, each a stream wait.
+ *  tg_capture_run: run graph g (static tasks only, a DAG of at most 65,536
+ *    tasks) as the CUDA graph Algorithm 1 builds with max_streams streams:
+ *    a re-arm, then per task (level by level) one kernel on its stream that
+ *    reads its input sum from its join word, runs the payload, writes its
+ *    output, count and digest, and adds its output to each successor's join
+ *    word; cross-stream edges become event waits.  Built on the first call
+ *    per (g, max_streams), replayed afterwards; *ns = device time of the
+ *    replay.  Results are read with tg_result_copy.  TG_ERR_INVALID for a
+ *    condition task, a cycle, more than 65,536 tasks or max_streams outside
+ *    1..32; TG_ERR_BUSY while g is in flight or the context serves. */
+int tg_levelize(uint32_t n, uint32_t m, const uint32_t *src, const uint32_t *dst, uint32_t *level,
+                uint32_t *index, uint32_t *n_levels);
+int tg_stream_plan(uint32_t n, uint32_t m, const uint32_t *src, const uint32_t *dst, uint32_t max_streams,
+                   uint32_t *stream, uint32_t *n_events, uint32_t *n_waits);
+int tg_capture_run(tg_ctx *ctx, tg_graph *g, uint32_t max_streams, uint64_t *ns);
+
 /* Run one graph without allocating anything (the paper has no counterpart:
  * this exists for callers that cannot allocate device memory, e.g. code
  * inside another framework's memory pool or a plugin handed fixed buffers).

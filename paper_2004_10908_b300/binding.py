@@ -101,6 +101,9 @@ SIGNATURES = {
     "tg_bench_payload": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "tg_bench_atomics": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(_u64)]),
     "tg_bench_chain": (ctypes.c_int, [_vp, _u32, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
+    "tg_levelize": (ctypes.c_int, [_u32, _u32, _vp, _vp, _vp, _vp, ctypes.POINTER(_u32)]),
+    "tg_stream_plan": (ctypes.c_int, [_u32, _u32, _vp, _vp, _u32, _vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
+    "tg_capture_run": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_u64)]),
     "tg_run_noalloc": (ctypes.c_int, [_u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]),
     "tg_trace_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "tg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -299,6 +302,37 @@ def tg_bench_payload(ctx, count, rounds):
     cs = _u32(0)
     _check(load().tg_bench_payload(_vp(ctx), count, rounds, ctypes.byref(ns), ctypes.byref(cs)), "tg_bench_payload")
     return ns.value, cs.value
+
+
+def tg_levelize(n, src, dst):
+    """Returns (status, level[n], index[n], n_levels) of the DAG (src[e] -> dst[e])."""
+    s, sp = _arr(src, np.uint32)
+    d, dp = _arr(dst, np.uint32)
+    level = np.zeros(n, np.uint32)
+    index = np.zeros(n, np.uint32)
+    nl = _u32(0)
+    st = load().tg_levelize(n, len(s), sp, dp, level.ctypes.data_as(_vp), index.ctypes.data_as(_vp),
+                            ctypes.byref(nl))
+    return st, level, index, nl.value
+
+
+def tg_stream_plan(n, src, dst, max_streams):
+    """Returns (status, stream[n], n_events, n_waits) of Algorithm 1's round-robin layout."""
+    s, sp = _arr(src, np.uint32)
+    d, dp = _arr(dst, np.uint32)
+    stream = np.zeros(n, np.uint32)
+    ne = _u32(0)
+    nw = _u32(0)
+    st = load().tg_stream_plan(n, len(s), sp, dp, max_streams, stream.ctypes.data_as(_vp), ctypes.byref(ne),
+                               ctypes.byref(nw))
+    return st, stream, ne.value, nw.value
+
+
+def tg_capture_run(ctx, g, max_streams):
+    """Returns (status, device ns of the replay)."""
+    ns = _u64(0)
+    st = load().tg_capture_run(_vp(ctx), _vp(g), max_streams, ctypes.byref(ns))
+    return st, ns.value
 
 
 def tg_bench_chain(ctx, hops, rounds):

@@ -118,6 +118,8 @@ struct tg_graph {
     cudaEvent_t ready = nullptr;  // instance set-up copies (null: nothing to wait for)
     u64 serve_ticket = 0;         // server mode: ticket of the submission in flight
     bool setup_pending = false;   // an instance whose descriptor / chunk table are not written yet
+    cudaGraphExec_t cap_exec = nullptr;   // capturer baseline (Algorithm 1), built for cap_streams
+    u32 cap_streams = 0;
 };
 
 struct tg_batch {
@@ -792,6 +794,8 @@ int tg_graph_destroy(tg_ctx *c, tg_graph *g)
         cudaEventSynchronize(g->ready);
         cudaEventDestroy(g->ready);
     }
+    if (g->cap_exec)
+        cudaGraphExecDestroy(g->cap_exec);
     c->nodes.release(g->chunk_off, g->n_chunks);
     if (g->edge_len)
         c->edge_pool.release(g->edge_off, g->edge_len);
@@ -980,6 +984,249 @@ int tg_result_copy(tg_ctx *c, const tg_graph *g, uint32_t *out, uint32_t *cnt, u
         if (total_execs)
             *total_execs = tot;
     }
+    return TG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// capturer baseline (Algorithm 1): levelize, round-robin streams, capture
+// ---------------------------------------------------------------------------
+namespace {
+
+// Longest-path levels of a DAG given as successor lists; index = position in
+// the level by ascending id.  False on a cycle.
+bool levelize_csr(u32 n, const std::vector<u32> &off, const std::vector<u32> &adj, std::vector<u32> &level,
+                  std::vector<u32> &index, u32 &n_levels)
+{
+    std::vector<u32> indeg(n, 0);
+    for (u32 e = 0; e < off[n]; ++e)
+        indeg[adj[e]]++;
+    level.assign(n, 0);
+    std::vector<u32> order;
+    order.reserve(n);
+    for (u32 v = 0; v < n; ++v)
+        if (indeg[v] == 0)
+            order.push_back(v);
+    for (size_t h = 0; h < order.size(); ++h) {
+        const u32 v = order[h];
+        for (u32 e = off[v]; e < off[v + 1]; ++e) {
+            const u32 t = adj[e];
+            level[t] = std::max(level[t], level[v] + 1u);
+            if (--indeg[t] == 0)
+                order.push_back(t);
+        }
+    }
+    if (order.size() != n)
+        return false;
+    n_levels = 0;
+    for (u32 v = 0; v < n; ++v)
+        n_levels = std::max(n_levels, level[v] + 1u);
+    std::vector<u32> fill(n_levels, 0);
+    index.assign(n, 0);
+    for (u32 v = 0; v < n; ++v)   // ascending id within each level
+        index[v] = fill[level[v]]++;
+    return true;
+}
+
+bool csr_from_edges(u32 n, u32 m, const u32 *src, const u32 *dst, std::vector<u32> &off, std::vector<u32> &adj)
+{
+    off.assign(n + 1, 0);
+    for (u32 e = 0; e < m; ++e) {
+        if (src[e] >= n || dst[e] >= n)
+            return false;
+        off[src[e] + 1]++;
+    }
+    for (u32 v = 0; v < n; ++v)
+        off[v + 1] += off[v];
+    adj.assign(m, 0);
+    std::vector<u32> cur(off.begin(), off.end() - 1);
+    for (u32 e = 0; e < m; ++e)
+        adj[cur[src[e]]++] = dst[e];
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tg_levelize(uint32_t n, uint32_t m, const uint32_t *src, const uint32_t *dst, uint32_t *level,
+                uint32_t *index, uint32_t *n_levels)
+{
+    if (n == 0 || !level || !index || (m && (!src || !dst)))
+        return TG_ERR_INVALID;
+    std::vector<u32> off, adj, lv, ix;
+    u32 nl = 0;
+    if (!csr_from_edges(n, m, src, dst, off, adj) || !levelize_csr(n, off, adj, lv, ix, nl))
+        return TG_ERR_INVALID;
+    std::copy(lv.begin(), lv.end(), level);
+    std::copy(ix.begin(), ix.end(), index);
+    if (n_levels)
+        *n_levels = nl;
+    return TG_OK;
+}
+
+int tg_stream_plan(uint32_t n, uint32_t m, const uint32_t *src, const uint32_t *dst, uint32_t max_streams,
+                   uint32_t *stream, uint32_t *n_events, uint32_t *n_waits)
+{
+    if (n == 0 || !stream || max_streams == 0 || max_streams > 32 || (m && (!src || !dst)))
+        return TG_ERR_INVALID;
+    std::vector<u32> off, adj, lv, ix;
+    u32 nl = 0;
+    if (!csr_from_edges(n, m, src, dst, off, adj) || !levelize_csr(n, off, adj, lv, ix, nl))
+        return TG_ERR_INVALID;
+    for (u32 v = 0; v < n; ++v)
+        stream[v] = ix[v] % max_streams;
+    u32 events = 0;
+    std::vector<std::pair<u32, u32>> cross;
+    for (u32 v = 0; v < n; ++v) {
+        bool rec = false;
+        for (u32 e = off[v]; e < off[v + 1]; ++e)
+            if (stream[adj[e]] != stream[v]) {
+                rec = true;
+                cross.emplace_back(v, adj[e]);
+            }
+        events += rec;
+    }
+    std::sort(cross.begin(), cross.end());
+    cross.erase(std::unique(cross.begin(), cross.end()), cross.end());
+    if (n_events)
+        *n_events = events;
+    if (n_waits)
+        *n_waits = (u32)cross.size();
+    return TG_OK;
+}
+
+int tg_capture_run(tg_ctx *c, tg_graph *g, uint32_t max_streams, uint64_t *ns)
+{
+    if (!c || !g || g->ctx != c || max_streams == 0 || max_streams > 32 || g->n > 65536u || g->n_cond != 0)
+        return TG_ERR_INVALID;
+    if (c->serving || graph_busy(g))
+        return TG_ERR_BUSY;
+    int rc = clear_if_dirty(c);
+    if (rc != TG_OK)
+        return rc;
+    if (g->setup_pending && (rc = instance_setup(c, g)) != TG_OK)
+        return rc;
+    if (g->ready)
+        TG_CUDA(cudaStreamWaitEvent(c->stream, g->ready, 0));
+    if (!g->cap_exec || g->cap_streams != max_streams) {
+        // the packed successor lists (graph-local ids) and task records, read back
+        const tg_graph *t = g->tmpl ? g->tmpl : g;
+        std::vector<NodeSlot> rec(g->n);
+        std::vector<u32> ed(t->m);
+        TG_CUDA(cudaStreamSynchronize(c->stream));
+        TG_CUDA(cudaMemcpy(rec.data(), c->edges + t->pristine_off, (size_t)g->n * sizeof(NodeSlot),
+                           cudaMemcpyDeviceToHost));
+        if (t->m)
+            TG_CUDA(cudaMemcpy(ed.data(), c->edges + t->edge_off, (size_t)t->m * 4, cudaMemcpyDeviceToHost));
+        std::vector<u32> off(g->n + 1, 0), adj(t->m);
+        for (u32 v = 0; v < g->n; ++v) {
+            const u32 cnt = rec[v].deg & 0xFFFFu;
+            const u64 first = rec[v].succ_off - t->edge_off;
+            if (first + cnt > t->m)
+                return TG_ERR_INTERNAL;
+            for (u32 j = 0; j < cnt; ++j)
+                adj[off[v] + j] = ed[first + j] & ~kSoleBit;
+            off[v + 1] = off[v] + cnt;
+        }
+        std::vector<u32> lv, ix;
+        u32 nl = 0;
+        if (!levelize_csr(g->n, off, adj, lv, ix, nl))
+            return TG_ERR_INVALID;
+        std::vector<std::vector<u32>> by_level(nl);
+        for (u32 v = 0; v < g->n; ++v)
+            by_level[lv[v]].push_back(v);
+        std::vector<std::vector<u32>> preds(g->n);
+        for (u32 v = 0; v < g->n; ++v)
+            for (u32 e = off[v]; e < off[v + 1]; ++e)
+                preds[adj[e]].push_back(v);
+        auto stream_of = [&](u32 v) { return ix[v] % max_streams; };
+
+        std::vector<cudaStream_t> S(max_streams, nullptr);
+        std::vector<cudaEvent_t> ev(g->n, nullptr);
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t fork = nullptr;
+        cudaError_t err = cudaSuccess;
+        auto chk = [&](cudaError_t e) {
+            if (err == cudaSuccess && e != cudaSuccess)
+                err = e;
+            return err == cudaSuccess;
+        };
+        for (u32 s = 0; s < max_streams; ++s)
+            chk(cudaStreamCreateWithFlags(&S[s], cudaStreamNonBlocking));
+        chk(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        for (u32 v = 0; v < g->n && err == cudaSuccess; ++v)
+            for (u32 e = off[v]; e < off[v + 1]; ++e)
+                if (stream_of(adj[e]) != stream_of(v)) {
+                    chk(cudaEventCreateWithFlags(&ev[v], cudaEventDisableTiming));
+                    break;
+                }
+        KParams p = base_params(c, c->geo);
+        p.lt = nullptr;
+        p.n_graphs = 1;
+        p.single_gid = g->gid;
+        p.max_n = g->n;
+        p.total_sources = g->n_src;
+        const u32 base = (u32)g->node_off;
+        if (chk(cudaStreamBeginCapture(S[0], cudaStreamCaptureModeThreadLocal))) {
+            chk(launch_rearm(p, S[0]));
+            chk(cudaEventRecord(fork, S[0]));
+            for (u32 s = 1; s < max_streams; ++s)
+                chk(cudaStreamWaitEvent(S[s], fork, 0));
+            for (u32 l = 0; l < nl && err == cudaSuccess; ++l)
+                for (u32 v : by_level[l]) {
+                    const u32 s = stream_of(v);
+                    for (u32 q : preds[v])
+                        if (stream_of(q) != s)
+                            chk(cudaStreamWaitEvent(S[s], ev[q], 0));
+                    chk(launch_capture_task(c->slots, c->outv, c->edges, base + v, base, S[s]));
+                    if (ev[v])
+                        chk(cudaEventRecord(ev[v], S[s]));
+                }
+            // join every stream back into the first before the capture ends
+            for (u32 s = 1; s < max_streams; ++s) {
+                cudaEvent_t j = nullptr;
+                if (chk(cudaEventCreateWithFlags(&j, cudaEventDisableTiming)) && chk(cudaEventRecord(j, S[s])))
+                    chk(cudaStreamWaitEvent(S[0], j, 0));
+                if (j)
+                    cudaEventDestroy(j);
+            }
+            cudaError_t e2 = cudaStreamEndCapture(S[0], &graph);
+            chk(e2);
+        }
+        if (err == cudaSuccess)
+            chk(cudaGraphInstantiate(&exec, graph, 0));
+        if (graph)
+            cudaGraphDestroy(graph);
+        for (cudaEvent_t e : ev)
+            if (e)
+                cudaEventDestroy(e);
+        if (fork)
+            cudaEventDestroy(fork);
+        for (cudaStream_t s : S)
+            if (s)
+                cudaStreamDestroy(s);
+        if (err != cudaSuccess) {
+            if (exec)
+                cudaGraphExecDestroy(exec);
+            return TG_ERR_CUDA;
+        }
+        if (g->cap_exec)
+            cudaGraphExecDestroy(g->cap_exec);
+        g->cap_exec = exec;
+        g->cap_streams = max_streams;
+    }
+    TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    TG_CUDA(cudaGraphLaunch(g->cap_exec, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    TG_CUDA(cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1));
+    if (ns)
+        *ns = (u64)((double)ms * 1e6);
+    c->timed = false;
     return TG_OK;
 }
 

@@ -160,5 +160,6 @@ size_t sched_dyn_smem(u32 smem_entries, u32 warps);
 cudaError_t launch_bench_payload(u64 count, u32 rounds, u32 *checksum, cudaStream_t st);
 cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink, cudaStream_t st);
 cudaError_t launch_bench_chain(u32 hops, u32 rounds, u32 *last, cudaStream_t st);
+cudaError_t launch_capture_task(NodeSlot *slots, u32 *outv, const u32 *edges, u32 u, u32 node_off, cudaStream_t st);
 
 }  // namespace tg

@@ -1219,6 +1219,24 @@ __global__ void bench_chain_kernel(u32 hops, u32 rounds, u32 *last)
     *last = x;
 }
 
+// One task of a captured DAG (Algorithm 1): its predecessors ran before it
+// on this or another stream, and each added its output to the task's join
+// word; the task runs once and passes its output on the same way.
+__global__ void capture_task_kernel(NodeSlot *slots, u32 *outv, const u32 *edges, u32 u, u32 node_off)
+{
+    const NodeSlot &s = slots[u];
+    const u32 succ_off = s.succ_off;
+    const u32 succ_cnt = s.deg & 0xFFFFu;
+    const u32 insum = (u32)(vld64(&slots[u].W) >> 32);
+    const u32 x = task_payload(s.lid, 0u, insum, s.prm & 0xFFFFu);
+    for (u32 j = threadIdx.x; j < succ_cnt; j += blockDim.x)
+        atomicAdd(&slots[node_off + (edges[succ_off + j] & ~kSoleBit)].W, (u64)x << 32);
+    if (threadIdx.x == 0) {
+        outv[u] = x;
+        *reinterpret_cast<uint2 *>(&slots[u].cnt) = make_uint2(1u, mix32(x));
+    }
+}
+
 // `count` returning 64-bit atomicAdd at pseudo-random words of a footprint.
 __global__ void bench_atomics_kernel(u64 *words, u64 footprint, u64 count, u64 *sink)
 {
@@ -1328,6 +1346,12 @@ cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink
 cudaError_t launch_bench_chain(u32 hops, u32 rounds, u32 *last, cudaStream_t st)
 {
     bench_chain_kernel<<<1, 1, 0, st>>>(hops, rounds, last);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_capture_task(NodeSlot *slots, u32 *outv, const u32 *edges, u32 u, u32 node_off, cudaStream_t st)
+{
+    capture_task_kernel<<<1, 32, 0, st>>>(slots, outv, edges, u, node_off);
     return cudaGetLastError();
 }
 

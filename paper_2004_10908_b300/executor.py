@@ -155,6 +155,11 @@ class Executor:
     def bench_chain(self, hops, rounds):
         return B.tg_bench_chain(self.ctx, hops, rounds)
 
+    def capture_run(self, gh: GraphHandle, max_streams: int):
+        """Run a static DAG as the CUDA graph of Algorithm 1 (one kernel per
+        task on round-robin streams); returns (status, device ns)."""
+        return B.tg_capture_run(self.ctx, gh.handle, max_streams)
+
     def close(self):
         if self.ctx:
             B.tg_ctx_destroy(self.ctx)
