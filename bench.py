@@ -314,6 +314,19 @@ def capturer_baseline(Executor, torch, B):
     return out
 
 
+def oracle_all_cores(graphs, what):
+    """The oracle as it stands, one instance per graph over every host core
+    (threads: the foreign call releases the GIL), on a bounded sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res = oracle.run_many(graphs, threads=cores)
+    dt = time.perf_counter() - t0
+    execs = sum(int(r.execs) for r in res)
+    return {"value": execs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{what}: {len(graphs)} graphs, {execs} executions, {dt:.2f} s"}
+
+
 def batched(Executor, torch):
     """4,096 graphs in one autotuned, CUDA-graph-captured launch vs one launch each."""
     t0 = time.time()
@@ -363,7 +376,8 @@ def batched(Executor, torch):
             "mean_rounds": mean_r,
             "autotuned": {k: chosen[k] for k in ("worker_blocks", "warps_per_block", "deque_depth",
                                                  "steal_policy", "max_steal", "max_thieves")},
-            "autotune_s": tune_s, "generate_s": gen_s}
+            "autotune_s": tune_s, "generate_s": gen_s,
+            "cpu_all_cores": oracle_all_cores(gs[::8], "every 8th graph of the batch")}
 
 
 def serving(Executor, torch):
@@ -411,6 +425,7 @@ def serving(Executor, torch):
                            "p99_ms": float(np.percentile(lat, 99) / 1e6),
                            "tasks_s": float(execs[which].sum() / wall)}
         out["p99_plain_over_served_1k"] = out["plain_1k"]["p99_ms"] / out["lambdas"][0]["p99_ms"]
+    out["cpu_all_cores"] = oracle_all_cores(gs, "the 64 request graphs, once each")
     return out
 
 
