@@ -1,0 +1,92 @@
+"""Composed graphs (module tasks) in the oracle, pinned: the paper's
+composition example with its outputs recomputed from the pinned payload,
+closed-form counts for modules in loops and nested modules, agreement with
+the C oracle when no module task is present, and error propagation."""
+import random
+
+import numpy as np
+
+import oracle
+import workloads as w
+from oracle import composed as oc
+from workloads.graphs import COND_LOOP, MODULE, STATIC, from_lists, pack_param
+
+R = 4
+
+
+def test_paper_composition_example():
+    """Composable Tasking example: taskflow1 = A -> B; taskflow2 = C -> D ->
+    E, E composed of taskflow1 (D is a static task here: subflows are not
+    part of this build)."""
+    tf1 = from_lists("taskflow1", [STATIC, STATIC], pack_param([R, R]), [(0, 1)])
+    tf2 = from_lists("taskflow2", [STATIC, STATIC, MODULE], pack_param([R, R, R]), [(0, 1), (1, 2)])
+    res = oc.run({"tf1": tf1, "tf2": tf2}, {"tf2": {2: "tf1"}}, "tf2")
+    st2, out2, cnt2, dig2, ex2 = res["tf2"]
+    st1, out1, cnt1, dig1, ex1 = res["tf1"]
+    assert st2 == oracle.OK and list(cnt2) == [1, 1, 1] and list(cnt1) == [1, 1]
+    c = oracle.payload(0, 0, 0, R)
+    d = oracle.payload(1, 0, c, R)
+    e = oracle.payload(2, 0, d, R)
+    a = oracle.payload(0, 0, e, R)      # the module's source receives E's output
+    b = oracle.payload(1, 0, a, R)
+    assert list(out2) == [c, d, e] and list(out1) == [a, b]
+    assert list(dig1) == [oracle.mix32(a), oracle.mix32(b)]
+
+
+def test_module_in_a_loop_runs_its_graph_each_time():
+    """I -> E (module of a 3-chain) -> C (loop, trip T) -> weak [E, X]."""
+    for T in (1, 2, 5, 9):
+        body = from_lists("chain3", [STATIC] * 3, pack_param([R] * 3), [(0, 1), (1, 2)])
+        top = from_lists("loop", [STATIC, MODULE, COND_LOOP, STATIC],
+                         [pack_param(R), pack_param(R), pack_param(R, T), pack_param(R)],
+                         [(0, 1), (1, 2), (2, 1), (2, 3)])
+        res = oc.run({"b": body, "t": top}, {"t": {1: "b"}}, "t")
+        st, out, cnt, dig, execs = res["t"]
+        assert st == oracle.OK and list(cnt) == [1, T, T, 1]
+        _, bout, bcnt, bdig, bexecs = res["b"]
+        assert list(bcnt) == [T, T, T] and bexecs == 3 * T
+        # last entry: the chain's input is E's output of its last execution
+        e_last = out[1]
+        x0 = oracle.payload(0, T - 1, e_last, R)
+        x1 = oracle.payload(1, T - 1, x0, R)
+        x2 = oracle.payload(2, T - 1, x1, R)
+        assert list(bout) == [x0, x1, x2]
+
+
+def test_nested_and_repeated_modules():
+    """g3: S -> M1 (composes g2) -> M2 (composes g2 again) -> Z;
+    g2: P -> N (composes g1) -> Q; g1: a diamond."""
+    g1 = w.diamond(R)
+    g2 = from_lists("g2", [STATIC, MODULE, STATIC], pack_param([R] * 3), [(0, 1), (1, 2)])
+    g3 = from_lists("g3", [STATIC, MODULE, MODULE, STATIC], pack_param([R] * 4), [(0, 1), (1, 2), (2, 3)])
+    res = oc.run({"g1": g1, "g2": g2, "g3": g3}, {"g3": {1: "g2", 2: "g2"}, "g2": {1: "g1"}}, "g3")
+    assert res["g3"][0] == oracle.OK
+    assert list(res["g3"][2]) == [1, 1, 1, 1]
+    assert list(res["g2"][2]) == [2, 2, 2]
+    assert list(res["g1"][2]) == [2, 2, 2, 2]
+    assert res["g1"][4] == 8
+
+
+def test_without_modules_equals_the_c_oracle():
+    rnd = random.Random(3)
+    graphs = [w.config1(levels=4, width=10, trip=3, rounds=8), w.do_while(7, 3)] + \
+             [w.nested_loops(s) for s in range(10)] + \
+             [w.config3(seed=3, n_cond=30, body_levels=3, body_width=4, rounds=4, trip_max=4)]
+    for g in graphs:
+        ref = oracle.run(g)
+        st, out, cnt, dig, execs = oc.run({"g": g}, {}, "g")["g"]
+        assert st == ref.status, g.name
+        if st == oracle.OK:
+            np.testing.assert_array_equal(cnt, ref.cnt, err_msg=g.name)
+            np.testing.assert_array_equal(out, ref.out, err_msg=g.name)
+            np.testing.assert_array_equal(dig, ref.dig, err_msg=g.name)
+            assert execs == ref.execs
+
+
+def test_errors_inside_a_module_end_the_run():
+    racy = w.pitfall_race()
+    top = from_lists("top", [STATIC, MODULE], pack_param([R, R]), [(0, 1)])
+    assert oracle.run(racy).status == oracle.RACE
+    assert oc.run({"r": racy, "t": top}, {"t": {1: "r"}}, "t")["t"][0] == oracle.RACE
+    loop = w.do_while(50, 1)
+    assert oc.run({"l": loop, "t": top}, {"t": {1: "l"}}, "t", exec_cap=40)["t"][0] == oracle.EXEC_LIMIT
