@@ -60,8 +60,16 @@ typedef struct tg_batch tg_batch;
  *   TG_COND_LOOP    0 (loop back) unless (iter+1) mod T == 0, then the exit
  *                   index: 1 if nsucc <= 2, else 1 + HC mod (nsucc-1)
  *   TG_COND_CONST   the constant; an index outside [0, nsucc) schedules
- *                   nothing (that control path ends). */
-enum { TG_STATIC = 0, TG_COND_BRANCH = 1, TG_COND_LOOP = 2, TG_COND_CONST = 3 };
+ *                   nothing (that control path ends).
+ * TG_MODULE (Composable Tasking; graphs made with tg_graph_create_composed):
+ * the task runs its payload, then the graph it composes runs to completion
+ * -- that graph's sources take the module task's output as their input sum,
+ * its tasks keep their counts and digests across entries within a run --
+ * and only then are the module task's successors released (strong edges)
+ * with its output.  Two module tasks must not use one graph at the same
+ * time: entering a graph that is in use ends the caller with TG_ERR_RACE;
+ * an error inside the composed graph becomes the caller's status. */
+enum { TG_STATIC = 0, TG_COND_BRANCH = 1, TG_COND_LOOP = 2, TG_COND_CONST = 3, TG_MODULE = 4 };
 
 enum {
     TG_OK = 0,
@@ -136,6 +144,20 @@ int tg_ctx_destroy(tg_ctx *ctx);
 int tg_graph_create(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
                     uint32_t n_edges, const uint32_t *src, const uint32_t *dst,
                     const uint8_t *weak, uint32_t seed, tg_graph **out);
+/* As tg_graph_create, with module tasks (Composable Tasking, "composed_of"):
+ * modules[n_nodes] names, for every TG_MODULE task, the graph it composes
+ * (NULL for every other task).  A composed graph belongs to the same
+ * context, is not an instance, and may itself compose others; it cannot be
+ * destroyed while a graph composing it exists (TG_ERR_BUSY).  A graph with
+ * module tasks runs with tg_run / tg_submit: each launch starts every graph
+ * it composes (transitively) from its initial state, and afterwards
+ * tg_result_copy on a composed graph reads its tasks' results.  Batches,
+ * instances, the resident server and tg_capture_run refuse graphs with
+ * module tasks (TG_ERR_INVALID).  TG_ERR_INVALID also for a module task
+ * without a graph, a graph given for another kind, or a foreign graph. */
+int tg_graph_create_composed(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
+                             uint32_t n_edges, const uint32_t *src, const uint32_t *dst,
+                             const uint8_t *weak, uint32_t seed, tg_graph *const *modules, tg_graph **out);
 int tg_graph_destroy(tg_ctx *ctx, tg_graph *g);
 
 typedef struct {

@@ -13,7 +13,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtg.so")
 
-TG_STATIC, TG_COND_BRANCH, TG_COND_LOOP, TG_COND_CONST = 0, 1, 2, 3
+TG_STATIC, TG_COND_BRANCH, TG_COND_LOOP, TG_COND_CONST, TG_MODULE = 0, 1, 2, 3, 4
 TG_OK, TG_PENDING = 0, 1
 TG_ERR_INVALID, TG_ERR_NO_SOURCE, TG_ERR_EDGE_KIND, TG_ERR_BUDGET = -1, -2, -3, -4
 TG_ERR_RACE, TG_ERR_EXEC_LIMIT, TG_ERR_TIMEOUT, TG_ERR_CANCELLED = -5, -6, -7, -8
@@ -76,6 +76,8 @@ SIGNATURES = {
                                      ctypes.POINTER(_vp)]),
     "tg_ctx_destroy": (ctypes.c_int, [_vp]),
     "tg_graph_create": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, ctypes.POINTER(_vp)]),
+    "tg_graph_create_composed": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, _vp,
+                                                ctypes.POINTER(_vp)]),
     "tg_graph_destroy": (ctypes.c_int, [_vp, _vp]),
     "tg_graph_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(tg_graph_info)]),
     "tg_run": (ctypes.c_int, [_vp, _vp]),
@@ -163,6 +165,24 @@ def tg_graph_create(ctx, kinds, params, src, dst, seed=0, weak=None):
     out = _vp()
     st = load().tg_graph_create(_vp(ctx), k.shape[0], kp, pp, s.shape[0], sp, dp, wp, seed & 0xFFFFFFFF,
                                 ctypes.byref(out))
+    return st, (out.value if st == TG_OK else None)
+
+
+def tg_graph_create_composed(ctx, kinds, params, src, dst, modules, seed=0, weak=None):
+    """modules: {task: graph handle} for the TG_MODULE tasks.  Returns (status, handle)."""
+    k, kp = _arr(kinds, np.uint8)
+    p, pp = _arr(params, np.uint32)
+    s, sp = _arr(src, np.uint32)
+    d, dp = _arr(dst, np.uint32)
+    wp = None
+    if weak is not None:
+        w, wp = _arr(weak, np.uint8)
+    table = (_vp * max(1, k.shape[0]))()
+    for v, h in modules.items():
+        table[int(v)] = h
+    out = _vp()
+    st = load().tg_graph_create_composed(_vp(ctx), k.shape[0], kp, pp, s.shape[0], sp, dp, wp, seed & 0xFFFFFFFF,
+                                         ctypes.cast(table, _vp), ctypes.byref(out))
     return st, (out.value if st == TG_OK else None)
 
 

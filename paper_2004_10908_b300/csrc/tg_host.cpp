@@ -120,6 +120,9 @@ struct tg_graph {
     bool setup_pending = false;   // an instance whose descriptor / chunk table are not written yet
     cudaGraphExec_t cap_exec = nullptr;   // capturer baseline (Algorithm 1), built for cap_streams
     u32 cap_streams = 0;
+    std::vector<tg_graph *> mods;         // graphs its module tasks compose (distinct)
+    u32 n_mod = 0;                        // module tasks
+    int n_refs = 0;                       // graphs whose module tasks compose this one
 };
 
 struct tg_batch {
@@ -554,21 +557,32 @@ int tg_ctx_get_opts(const tg_ctx *c, tg_ctx_opts *o)
     return TG_OK;
 }
 
-int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t *params, uint32_t m,
-                    const uint32_t *src, const uint32_t *dst, const uint8_t *weak, uint32_t seed, tg_graph **out)
+static bool is_cond(u32 kind) { return kind >= TG_COND_BRANCH && kind <= TG_COND_CONST; }
+
+static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t *params, uint32_t m,
+                        const uint32_t *src, const uint32_t *dst, const uint8_t *weak, uint32_t seed,
+                        tg_graph *const *modules, tg_graph **out)
 {
     if (!c || !out || n == 0 || !kinds || !params || (m && (!src || !dst)))
         return TG_ERR_INVALID;
     *out = nullptr;
     const u64 t0 = now_ns();
     // ---- validation (same order as the rule statement in tg.h)
-    u32 n_cond = 0;
+    u32 n_cond = 0, n_mod = 0;
     for (u32 v = 0; v < n; ++v) {
-        if (kinds[v] > TG_COND_CONST)
+        if (kinds[v] > TG_MODULE || (kinds[v] == TG_MODULE && !modules))
             return TG_ERR_INVALID;
         if (kinds[v] == TG_COND_LOOP && ((params[v] >> 16) & 0xFFu) == 0u)
             return TG_ERR_INVALID;
-        n_cond += kinds[v] != TG_STATIC;
+        if (modules) {
+            const tg_graph *mg = modules[v];
+            if ((kinds[v] == TG_MODULE) != (mg != nullptr))
+                return TG_ERR_INVALID;
+            if (mg && (mg->ctx != c || mg->tmpl != nullptr))
+                return TG_ERR_INVALID;
+        }
+        n_cond += is_cond(kinds[v]);
+        n_mod += kinds[v] == TG_MODULE;
     }
     for (u32 e = 0; e < m; ++e)
         if (src[e] >= n || dst[e] >= n)
@@ -576,20 +590,20 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
     std::vector<u32> outdeg(n, 0), sin(n, 0), win(n, 0);
     for (u32 e = 0; e < m; ++e) {
         outdeg[src[e]]++;
-        if (kinds[src[e]] == TG_STATIC)
+        if (!is_cond(kinds[src[e]]))
             sin[dst[e]]++;
         else
             win[dst[e]]++;
     }
     for (u32 v = 0; v < n; ++v) {
-        if (kinds[v] != TG_STATIC && outdeg[v] == 0)
+        if (is_cond(kinds[v]) && outdeg[v] == 0)
             return TG_ERR_INVALID;
         if (outdeg[v] > kMaxDegree || sin[v] > kMaxDegree)
             return TG_ERR_INVALID;
     }
     if (weak)
         for (u32 e = 0; e < m; ++e)
-            if ((weak[e] != 0) != (kinds[src[e]] != TG_STATIC))
+            if ((weak[e] != 0) != is_cond(kinds[src[e]]))
                 return TG_ERR_EDGE_KIND;
     u32 n_src = 0;
     for (u32 v = 0; v < n; ++v)
@@ -600,7 +614,7 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
     // ---- pool space: a chunk-aligned execution range, and in the edge pool
     // the successor lists, the sources and the pristine record image
     const u64 n_chunks = ((u64)n + kChunk - 1) >> kChunkShift;
-    const u64 bytes = n_chunks * kChunk * 36 + ((u64)m + n_src + 64 + 8ull * n) * 4;
+    const u64 bytes = n_chunks * kChunk * 36 + ((u64)m + n_mod + n_src + 64 + 8ull * n) * 4;
     if (c->used + bytes > c->budget || c->free_gids.empty())
         return TG_ERR_BUDGET;
     tg_graph *g = new (std::nothrow) tg_graph();
@@ -614,7 +628,8 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
     g->node_off = g->chunk_off << kChunkShift;
     // the pristine image starts on a 256-byte boundary (64 entries), so its
     // device-to-device copies stay on the copy engines
-    const u64 lead = (u64)m + n_src;
+    // a module task's list is led by the slot id of the graph it composes
+    const u64 lead = (u64)m + n_mod + n_src;
     g->edge_len = lead + 64 + 8ull * n;
     if (!c->edge_pool.alloc(g->edge_len, g->edge_off)) {
         c->nodes.release(g->chunk_off, n_chunks);
@@ -630,6 +645,7 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
     g->m = m;
     g->n_src = n_src;
     g->n_cond = n_cond;
+    g->n_mod = n_mod;
     g->seed = seed;
     g->bytes = bytes;
 
@@ -664,16 +680,24 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
         s.cnt = 0;
         s.dig = 0;
         memcpy(&hs[v], &s, sizeof(s));
+        if (kind == TG_MODULE)
+            he[acc++] = modules[v]->gid;
         outdeg[v] = acc;   // reuse as the fill cursor
         acc += (u32)(s.deg & 0xFFFFu);
     }
-    // a static task's edge to a task with no other strong in-edge is marked:
-    // its release needs no join-word update
+    // a strong edge to a task with no other strong in-edge is marked: its
+    // release needs no join-word update
     for (u32 e = 0; e < m; ++e)
-        he[outdeg[src[e]]++] = dst[e] | ((kinds[src[e]] == TG_STATIC && sin[dst[e]] == 1u) ? kSoleBit : 0u);
+        he[outdeg[src[e]]++] = dst[e] | ((!is_cond(kinds[src[e]]) && sin[dst[e]] == 1u) ? kSoleBit : 0u);
     for (u32 v = 0, k = 0; v < n; ++v)
         if (sin[v] == 0 && win[v] == 0)
-            he[m + k++] = v;
+            he[m + n_mod + k++] = v;
+    if (modules)
+        for (u32 v = 0; v < n; ++v)
+            if (modules[v] && std::find(g->mods.begin(), g->mods.end(), modules[v]) == g->mods.end()) {
+                g->mods.push_back(modules[v]);
+                modules[v]->n_refs++;
+            }
     for (u64 k = 0; k < n_chunks; ++k)
         hc[k] = g->gid;
     const u64 t1 = now_ns();
@@ -684,7 +708,8 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
     d.seed = seed;
     d.node_off = (u32)g->node_off;
     d.n = n;
-    d.src_off = edge_base + m;
+    d.src_off = edge_base + m + n_mod;
+    d.ret = kEmpty32;
     d.n_src = n_src;
     d.exec_cap = (u32)std::min<u64>(c->opts.exec_cap, 0xFFFFFFFFull);
     memcpy(c->h_stage + edge_bytes + chunk_bytes, &d, sizeof(d));
@@ -703,6 +728,21 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
     g->upload_ns = now_ns() - t1;
     *out = g;
     return TG_OK;
+}
+
+int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t *params, uint32_t m,
+                    const uint32_t *src, const uint32_t *dst, const uint8_t *weak, uint32_t seed, tg_graph **out)
+{
+    return graph_create(c, n, kinds, params, m, src, dst, weak, seed, nullptr, out);
+}
+
+int tg_graph_create_composed(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t *params, uint32_t m,
+                             const uint32_t *src, const uint32_t *dst, const uint8_t *weak, uint32_t seed,
+                             tg_graph *const *modules, tg_graph **out)
+{
+    if (!modules)
+        return TG_ERR_INVALID;
+    return graph_create(c, n, kinds, params, m, src, dst, weak, seed, modules, out);
 }
 
 }  // extern "C"
@@ -735,7 +775,7 @@ extern "C" {
 
 int tg_instance_create(tg_ctx *c, tg_graph *t, tg_graph **out)
 {
-    if (!c || !t || !out || t->ctx != c)
+    if (!c || !t || !out || t->ctx != c || t->n_mod)
         return TG_ERR_INVALID;
     *out = nullptr;
     tg_graph *src = t->tmpl ? t->tmpl : t;
@@ -786,8 +826,8 @@ int tg_graph_destroy(tg_ctx *c, tg_graph *g)
 {
     if (!c || !g || g->ctx != c)
         return TG_ERR_INVALID;
-    if (g->n_inst > 0 || g->serve_ticket != 0)
-        return TG_ERR_BUSY;   // instances still use its packed form, or it is being served
+    if (g->n_inst > 0 || g->serve_ticket != 0 || g->n_refs > 0)
+        return TG_ERR_BUSY;   // instances still use its packed form, it is being served or composed
     if (g->busy)
         cudaEventSynchronize(g->busy);
     if (g->ready) {
@@ -796,6 +836,8 @@ int tg_graph_destroy(tg_ctx *c, tg_graph *g)
     }
     if (g->cap_exec)
         cudaGraphExecDestroy(g->cap_exec);
+    for (tg_graph *mg : g->mods)
+        mg->n_refs--;
     c->nodes.release(g->chunk_off, g->n_chunks);
     if (g->edge_len)
         c->edge_pool.release(g->edge_off, g->edge_len);
@@ -837,7 +879,7 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     if (!c || !g || g->ctx != c || !ticket)
         return TG_ERR_INVALID;
     if (c->serving)
-        return serve_submit(c, g, ticket);
+        return g->n_mod ? TG_ERR_INVALID : serve_submit(c, g, ticket);
     if (graph_busy(g))
         return TG_ERR_BUSY;
     int rc = clear_if_dirty(c);
@@ -856,6 +898,24 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     p.single_gid = g->gid;
     p.max_n = g->n;
     p.total_sources = g->n_src;
+    if (g->n_mod) {
+        // every graph the composition reaches starts idle from its initial state
+        std::vector<tg_graph *> todo(g->mods.begin(), g->mods.end()), seen;
+        while (!todo.empty()) {
+            tg_graph *mg = todo.back();
+            todo.pop_back();
+            if (mg == g || std::find(seen.begin(), seen.end(), mg) != seen.end())
+                continue;
+            seen.push_back(mg);
+            todo.insert(todo.end(), mg->mods.begin(), mg->mods.end());
+        }
+        p.has_modules = 1u;
+        for (tg_graph *mg : seen) {
+            if (mg->ready)
+                TG_CUDA(cudaStreamWaitEvent(c->stream, mg->ready, 0));
+            TG_CUDA(launch_module_rearm(p, mg->gid, mg->n, c->stream));
+        }
+    }
     Submission s;
     s.g = g;
     TG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
@@ -972,7 +1032,7 @@ int tg_result_copy(tg_ctx *c, const tg_graph *g, uint32_t *out, uint32_t *cnt, u
         TG_CUDA(cudaStreamSynchronize(c->side));
         u64 tot = 0;
         for (u32 v = 0; v < g->n; ++v) {
-            const u32 k = tmp[v].cnt & ~kInflight;
+            const u32 k = tmp[v].cnt & ~(kInflight | kAwait);
             if (cnt)
                 cnt[v] = k;
             if (dig)
@@ -1099,7 +1159,8 @@ int tg_stream_plan(uint32_t n, uint32_t m, const uint32_t *src, const uint32_t *
 
 int tg_capture_run(tg_ctx *c, tg_graph *g, uint32_t max_streams, uint64_t *ns)
 {
-    if (!c || !g || g->ctx != c || max_streams == 0 || max_streams > 32 || g->n > 65536u || g->n_cond != 0)
+    if (!c || !g || g->ctx != c || max_streams == 0 || max_streams > 32 || g->n > 65536u || g->n_cond != 0 ||
+        g->n_mod != 0)
         return TG_ERR_INVALID;
     if (c->serving || graph_busy(g))
         return TG_ERR_BUSY;
@@ -1276,7 +1337,7 @@ int tg_batch_create(tg_ctx *c, tg_graph *const *gs, uint32_t n, tg_batch **out)
     u64 inj = 0;
     u32 max_n = 0;
     for (u32 i = 0; i < n; ++i) {
-        if (!gs[i] || gs[i]->ctx != c)
+        if (!gs[i] || gs[i]->ctx != c || gs[i]->n_mod)
             return TG_ERR_INVALID;
         for (u32 j = 0; j < i; ++j)
             if (gs[j] == gs[i])

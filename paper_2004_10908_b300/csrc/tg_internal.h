@@ -35,7 +35,8 @@ struct alignas(64) GDesc {
     u32 src_off;    // source list in the edge pool
     u32 n_src;
     u32 exec_cap;
-    u32 pad[7];
+    u32 ret;        // composed graph in use: the module task to resume when it completes (else kEmpty32)
+    u32 pad[6];
 };
 static_assert(sizeof(GDesc) == 64, "GDesc is 64 bytes");
 
@@ -102,6 +103,7 @@ constexpr u32 kEmpty32 = 0xFFFFFFFFu;
 constexpr u64 kEmpty = 0xFFFFFFFFFFFFFFFFull;
 constexpr u32 kStrongBit = 0x80000000u;   // in a ready entry's low word
 constexpr u32 kInflight = 0x80000000u;    // in NodeSlot::cnt
+constexpr u32 kAwait = 0x40000000u;       // in NodeSlot::cnt: a module task waits for its composed graph
 constexpr u32 kMaxNodeIndex = 0x7FFFFFFEu;
 constexpr u32 kSoleBit = 0x80000000u;     // in a static task's successor id: the target has
                                           // strong in-degree 1 (its join word is never used)
@@ -138,6 +140,8 @@ struct KParams {
     u32 batch_max;         // activations a warp takes per step (1..32)
     u32 local_keep;        // shared-memory ring size above which new work goes public (0 = default)
     u32 thief_mode;        // 0 capped thief slots, 1 adaptive (parks and wake tickets)
+    u32 has_modules;       // the launch's graphs compose other graphs (module tasks)
+    u32 pad5;
     u32 *thief_slots;      // max_thieves words, each on its own 128-byte line
     u64 time_limit_ns;
     u64 *trace;            // TG_OPT_TRACE: per task {start ns, publish ns} (may be null)
@@ -152,6 +156,7 @@ struct KParams {
 
 // Launch helpers implemented in tg_kernels.cu (all enqueue on `st`).
 cudaError_t launch_rearm(const KParams &p, cudaStream_t st);
+cudaError_t launch_module_rearm(const KParams &p, u32 gid, u32 n, cudaStream_t st);
 cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t st, bool serve = false);
 cudaError_t launch_finalize(const KParams &p, cudaStream_t st);
 cudaError_t launch_clear(u64 *slots, size_t count, cudaStream_t st);

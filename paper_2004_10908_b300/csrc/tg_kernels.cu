@@ -259,16 +259,26 @@ __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u6
 // Examine the result of the previous iteration's pending-count update: a
 // graph whose pending count reached zero is complete; one whose execution
 // count passed its cap is poisoned with TG_ERR_EXEC_LIMIT.
-template <bool kServe>
-__device__ __forceinline__ void settle_finish(const KParams &p, bool &pend, u64 old, u64 delta, u32 g, u32 cap)
+template <bool kServe, bool kMod>
+__device__ __forceinline__ u64 settle_finish(const KParams &p, bool &pend, u64 old, u64 delta, u32 g, u32 cap)
 {
     if (!pend)
-        return;
+        return kEmpty;
+    u64 cont = kEmpty;
     const u64 nw = old + delta;
     if ((u32)(nw >> 32) > cap)
         atomicCAS(&p.descs[g].status, 0, TG_ERR_EXEC_LIMIT);
     if ((u32)nw == 0u) {
-        if (kServe) {
+        const u32 ret = (!kServe && kMod) ? vld32(&p.descs[g].ret) : kEmpty32;
+        if (ret != kEmpty32) {
+            // a composed graph is done: its module task resumes (a
+            // continuation activation) and inherits its status
+            const i32 st = vldi(&p.descs[g].status);
+            if (st != 0)
+                atomicCAS(&p.descs[__ldg(&p.chunk_gid[ret >> kChunkShift])].status, 0, st);
+            vst32(&p.descs[g].ret, kEmpty32);
+            cont = (u64)ret;
+        } else if (kServe) {
             // the graph is done: post a completion record to the host
             fence_acq_rel_gpu();
             const i32 st = vldi(&p.descs[g].status);
@@ -280,6 +290,7 @@ __device__ __forceinline__ void settle_finish(const KParams &p, bool &pend, u64 
         }
     }
     pend = false;
+    return cont;
 }
 
 // Loads of data that is immutable while its graph exists: through L1 for a
@@ -324,8 +335,11 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
     }
 }
 
-template <bool kServe>
-__global__ void sched_kernel(KParams p)
+// kMod: the launch's graphs have module tasks (a separate variant, so that
+// launches without them carry none of that code).  At most 512 threads (16
+// worker warps): 128 registers per thread fill the SM.
+template <bool kServe, bool kMod>
+__global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
 {
     extern __shared__ u64 s_ring[];
     __shared__ u32 s_head, s_tail;
@@ -356,7 +370,9 @@ __global__ void sched_kernel(KParams p)
 
     const bool race_check = (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
     const int bmax = (int)min(32u, max(1u, p.batch_max));
-    const bool single = !kServe && p.lt == nullptr;   // one graph: every activation has gid == single_gid
+    // one graph: every activation has gid == single_gid (not when it composes others)
+    const bool single = !kServe && !kMod && p.lt == nullptr;
+    constexpr bool modules = !kServe && kMod;
     const u32 single_cap = single ? ld_imm<kServe>(&p.descs[p.single_gid].exec_cap) : 0u;
     const u64 t0 = globaltimer();
     const u64 deadline = t0 + p.time_limit_ns;
@@ -375,6 +391,16 @@ __global__ void sched_kernel(KParams p)
     w.err = 0;
     w.avail_word = &p.ctl->avail[blockIdx.x >> 5];
     w.avail_bit = 1u << (blockIdx.x & 31u);
+    // a composed graph's completion resumes its module task: published after a fence
+    auto resume = [&](u64 cont, u64 &spill_ctr) {
+        if (!modules)
+            return;
+        const bool h = cont != kEmpty;
+        if (__ballot_sync(kFull, h) != 0u) {
+            fence_acq_rel_gpu();
+            emit(w, h, cont, lane, spill_ctr);
+        }
+    };
     u32 *my_push = s_push + warp * 32;
     u32 *my_keep = s_keep + warp * 32;
     u64 *my_stage = s_ring + ring_n + (size_t)warp * kStage;
@@ -426,7 +452,7 @@ __global__ void sched_kernel(KParams p)
             if (k) {
                 st_local++;
             } else {
-                settle_finish<kServe>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+                resume(settle_finish<kServe, kMod>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
                 if (adaptive && busy_w) {
                     busy_w = false;
                     if (lane == 0 && atomicSub(&s_busy, 1u) == 1u)
@@ -723,21 +749,25 @@ __global__ void sched_kernel(KParams p)
                 c_age++;
             }
         }
-        const u32 succ_off = imm.x;
+        // a module task's list starts with the slot id of the graph it composes
+        const u32 succ_off = imm.x + ((modules && ((imm.z >> 16) & 0xFFu) == TG_MODULE) ? 1u : 0u);
         const u32 succ_cnt = imm.y & 0xFFFFu;
         const u32 indeg = imm.y >> 16;
         const u32 rounds = imm.z & 0xFFFFu;
         const u32 kind = (imm.z >> 16) & 0xFFu;
         const u32 arg = imm.z >> 24;
         const u32 lid = imm.w;
-        const u32 iter = stt.x & ~kInflight;
+        const u32 iter = stt.x & ~(kInflight | kAwait);
+        // a module task whose composed graph finished: release its successors
+        const bool cont = modules && act && kind == TG_MODULE && (stt.x & kAwait) != 0u;
+        const bool enter = modules && act && kind == TG_MODULE && !cont;
 
         // Successor ids of static tasks are fetched before the payload runs,
         // so their latency hides under it.  If no lane has more than
         // kPerLaneMax successors each lane releases its own; otherwise the
         // edges are flattened over the warp (edge e belongs to the lane
         // whose exclusive prefix covers it) to spread a wide fan-out.
-        const u32 c = (act && kind == TG_STATIC) ? succ_cnt : 0u;
+        const u32 c = (act && (kind == TG_STATIC || cont)) ? succ_cnt : 0u;
         const u32 maxc = __reduce_max_sync(kFull, c);
         const bool per_lane = maxc <= kPerLaneMax;
         if (traced) {
@@ -794,7 +824,7 @@ __global__ void sched_kernel(KParams p)
         }
 
         // the previous iteration's pending-count update arrives meanwhile
-        settle_finish<kServe>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+        resume(settle_finish<kServe, kMod>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
 
         // a strong activation consumed its join word: re-arm it for the next
         // round (composes with releases of that round that arrive early)
@@ -804,15 +834,15 @@ __global__ void sched_kernel(KParams p)
         if (p.trace && act)
             p.trace[2ull * u] = globaltimer();
         // ---- payload
-        const u32 x = act ? task_payload(lid, iter, insum, rounds) : 0u;
-        const u32 dg = mix32(stt.y ^ x);
+        const u32 x = cont ? __ldcg(&p.outv[u]) : (act ? task_payload(lid, iter, insum, rounds) : 0u);
+        const u32 dg = cont ? stt.y : mix32(stt.y ^ x);
         if (traced) {
             asm volatile("" ::"r"(dg));
             mark(2);
         }
 
         const bool run = act && c_status == 0;
-        const u32 U = run ? (kind == TG_STATIC ? succ_cnt : 1u) : 0u;
+        const u32 U = run ? ((kind == TG_STATIC || cont) ? succ_cnt : 1u) : 0u;
         // reserve the pending count of every activation this warp may push
         // before any of them becomes visible (a fence precedes publication)
         if (single) {
@@ -832,13 +862,14 @@ __global__ void sched_kernel(KParams p)
                 rem &= ~m;
             }
         }
-        if (run)
+        if (run && !cont)
             st_tasks++;
         if (!race_check) {
             // without in-flight flags the state must be visible before any
             // release makes a later activation of this task possible
             if (run)
-                __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt), make_uint2(iter + 1u, dg));
+                __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt),
+                       make_uint2(cont ? iter : ((iter + 1u) | (enter ? kAwait : 0u)), dg));
             fence_acq_rel_gpu();
         }
         if (!per_lane) {
@@ -860,7 +891,7 @@ __global__ void sched_kernel(KParams p)
         // ---- condition tasks: jump to successors[r]
         bool c_has = false;
         u32 c_t = 0, c_fl = 0;
-        if (run && kind != TG_STATIC) {
+        if (run && kind >= TG_COND_BRANCH && kind <= TG_COND_CONST) {
             int r = cond_index(kind, arg, c_seed, lid, iter, succ_cnt);
             if (r >= 0 && (u32)r < succ_cnt) {
                 c_t = c_base + (ld_imm<kServe>(&p.edges[succ_off + (u32)r]) & ~kSoleBit);
@@ -995,20 +1026,68 @@ __global__ void sched_kernel(KParams p)
         if (racy != kEmpty32)
             atomicCAS(&p.descs[racy].status, 0, TG_ERR_RACE);
 
+        if (enter && run)
+            mp++;   // a module task's continuation: pushed when its graph completes
+
         // ---- release own in-flight flags (with the new count and digest).
         // The fence orders them before the publication of new work; a step
         // that publishes nothing (it keeps its output in hand) leaves it to
         // the next step that does.  The server always fences: the host reads
-        // its completion records while it runs.
+        // its completion records while it runs.  A module task keeps its flag
+        // (and marks itself waiting) until its continuation has run.
+        const bool any_enter = modules && __any_sync(kFull, enter && run);
         if (race_check) {
             if (run)
                 __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt),
-                       make_uint2((iter + 1u) | (keep_self ? kInflight : 0u), dg));
-            if (kServe || ns > kHandMax)
+                       make_uint2((cont ? iter : iter + 1u) | (keep_self ? kInflight : 0u) |
+                                      (enter ? (kInflight | kAwait) : 0u),
+                                  dg));
+            if (kServe || ns > kHandMax || any_enter)
                 fence_acq_rel_gpu();
+        } else if (any_enter) {
+            fence_acq_rel_gpu();
         }
-        if (run)
+        if (run && !cont)
             __stcs(&p.outv[u], x);
+        if (any_enter) {
+            // ---- a module task enters its composed graph: takes it (its
+            // pending count must be idle, else two module tasks use it at
+            // once: a race), names itself as the task to resume, and -- after
+            // a fence -- activates the graph's sources with its output.  A
+            // refused entry resumes at once.
+            bool entered = false;
+            u32 m_base = 0, m_src = 0, m_nsrc = 0;
+            if (enter && run) {
+                const u32 mg = ld_imm<kServe>(&p.edges[imm.x]);
+                m_nsrc = ld_imm<kServe>(&p.descs[mg].n_src);
+                m_src = ld_imm<kServe>(&p.descs[mg].src_off);
+                m_base = ld_imm<kServe>(&p.descs[mg].node_off);
+                const u64 was = atomicAdd(&p.descs[mg].pe, (u64)m_nsrc);
+                if ((u32)was == 0u) {
+                    vst32(&p.descs[mg].ret, u);
+                    entered = true;
+                } else {
+                    atomicAdd(&p.descs[mg].pe, (u64)0 - (u64)m_nsrc);
+                    atomicCAS(&p.descs[gid].status, 0, TG_ERR_RACE);
+                }
+            }
+            fence_acq_rel_gpu();
+            emit(w, enter && run && !entered, (u64)u, lane, st_spill);
+            u32 rem = __ballot_sync(kFull, entered);
+            while (rem) {
+                const int l = __ffs(rem) - 1;
+                rem &= rem - 1u;
+                const u32 nb = __shfl_sync(kFull, m_base, l);
+                const u32 so = __shfl_sync(kFull, m_src, l);
+                const u32 nn = __shfl_sync(kFull, m_nsrc, l);
+                const u32 xv = __shfl_sync(kFull, x, l);
+                for (u32 i = 0; i < nn; i += 32u) {
+                    const bool h = i + (u32)lane < nn;
+                    const u64 ent = h ? (((u64)xv << 32) | (u64)(nb + __ldcg(&p.edges[so + i + (u32)lane]))) : 0ull;
+                    emit(w, h, ent, lane, st_spill);
+                }
+            }
+        }
         if (p.trace && act)
             p.trace[2ull * u + 1ull] = globaltimer();
         // ---- a warp whose step produced at most kHandMax activations runs
@@ -1035,7 +1114,7 @@ __global__ void sched_kernel(KParams p)
                 const u32 sumU = __reduce_add_sync(kFull, U);
                 if (lane == 0 && E) {
                     const long long d = (long long)sumP - (long long)sumU - (long long)E;
-                    pend_delta = ((u64)E << 32) + (u64)d;
+                    pend_delta = ((u64)E << 32) + (u64)d;   // (no continuations without modules)
                     pend_old = atomicAdd(&p.descs[p.single_gid].pe, pend_delta);
                     pend_g = p.single_gid;
                     pend_cap = single_cap;
@@ -1048,12 +1127,14 @@ __global__ void sched_kernel(KParams p)
                     u32 g = __shfl_sync(kFull, gid, l);
                     bool in = act && gid == g;
                     u32 m = __ballot_sync(kFull, in);
+                    // a continuation consumes its pending count but is no execution
+                    u32 mx = __ballot_sync(kFull, in && !cont);
                     u32 sumP = __reduce_add_sync(kFull, in ? P : 0u);
                     u32 sumU = __reduce_add_sync(kFull, in ? U : 0u);
                     if (lane == l) {
                         const u32 E = (u32)__popc(m);
                         const long long d = (long long)sumP - (long long)sumU - (long long)E;
-                        pend_delta = ((u64)E << 32) + (u64)d;
+                        pend_delta = ((u64)__popc(mx) << 32) + (u64)d;
                         pend_old = atomicAdd(&p.descs[g].pe, pend_delta);
                         pend_g = g;
                         pend_cap = c_cap;
@@ -1085,7 +1166,7 @@ __global__ void sched_kernel(KParams p)
         }
     }
 
-    settle_finish<kServe>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+    (void)settle_finish<kServe, kMod>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
     if (lane == 0) {
         atomicAdd(&s_stats[ST_POP_LOCAL], st_local);
         atomicAdd(&s_stats[ST_POP_OWN], st_own);
@@ -1135,6 +1216,7 @@ __global__ void rearm_kernel(KParams p)
         if (threadIdx.x == 0) {
             D.pe = (u64)D.n_src;
             D.status = 0;
+            D.ret = kEmpty32;
         }
     }
     if (gi == 0 && blockIdx.x == 0) {
@@ -1160,6 +1242,26 @@ __global__ void rearm_kernel(KParams p)
             if (p.cancel)
                 *p.cancel = 0u;
         }
+    }
+}
+
+// A graph composed by a module task of the launch: its state starts from
+// scratch, idle (nothing pending, no module task to resume), sources not
+// activated -- its module task does that.
+__global__ void module_rearm_kernel(KParams p, u32 gid, u32 n)
+{
+    GDesc &D = p.descs[gid];
+    const u32 off = D.node_off;
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const u32 u = off + i;
+        p.slots[u].W = (u64)(p.slots[u].deg >> 16);
+        *reinterpret_cast<uint2 *>(&p.slots[u].cnt) = make_uint2(0u, 0u);
+        p.outv[u] = 0u;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        D.pe = 0ull;
+        D.status = 0;
+        D.ret = kEmpty32;
     }
 }
 
@@ -1274,18 +1376,29 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dyn_smem > raised[dev]) {
-            e = cudaFuncSetAttribute(sched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            e = cudaFuncSetAttribute(sched_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
-            e = cudaFuncSetAttribute(sched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            e = cudaFuncSetAttribute(sched_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            if (e != cudaSuccess)
+                return e;
+            e = cudaFuncSetAttribute(sched_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
             raised[dev] = dyn_smem;
         }
     }
     if (serve)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<true>, threads, dyn_smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false>, threads, dyn_smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<true, false>, threads, dyn_smem);
+    // the variant with module tasks must fit the same block shape
+    int with_mod = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&with_mod, sched_kernel<false, true>, threads, dyn_smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false, false>, threads, dyn_smem);
+    if (e == cudaSuccess)
+        *blocks_per_sm = std::min(*blocks_per_sm, with_mod);
+    return e;
 }
 
 cudaError_t launch_rearm(const KParams &p, cudaStream_t st)
@@ -1297,13 +1410,23 @@ cudaError_t launch_rearm(const KParams &p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+cudaError_t launch_module_rearm(const KParams &p, u32 gid, u32 n, cudaStream_t st)
+{
+    const u32 blocks = n ? min((n + 255u) / 256u, 4096u) : 1u;
+    module_rearm_kernel<<<blocks, 256, 0, st>>>(p, gid, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t st, bool serve)
 {
     const size_t smem = sched_dyn_smem(p.smem_mask + 1u, (u32)threads / 32u);
     if (serve)
-        sched_kernel<true><<<blocks, threads, smem, st>>>(p);
+        sched_kernel<true, false><<<blocks, threads, smem, st>>>(p);
     else
-        sched_kernel<false><<<blocks, threads, smem, st>>>(p);
+        if (p.has_modules)
+            sched_kernel<false, true><<<blocks, threads, smem, st>>>(p);
+        else
+            sched_kernel<false, false><<<blocks, threads, smem, st>>>(p);
     return cudaGetLastError();
 }
 

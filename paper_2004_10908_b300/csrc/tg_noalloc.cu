@@ -167,7 +167,7 @@ __global__ void na_gather_kernel(u32 n, unsigned char *base, u32 *out, u32 *cnt,
         if (out)
             out[v] = outv[v];
         if (cnt)
-            cnt[v] = slots[v].cnt & ~kInflight;
+            cnt[v] = slots[v].cnt & ~(kInflight | kAwait);
         if (dig)
             dig[v] = slots[v].dig;
     }

@@ -75,9 +75,16 @@ class Executor:
             raise B.TgError(st, f"tg_graph_create {name}")
         return GraphHandle(self, h, len(kinds), len(src), name)
 
-    def graph(self, g, weak=None):
-        """Upload a workloads.Graph-like object (kinds, params, src, dst, seed)."""
-        return self.create(g.kinds, g.params, g.src, g.dst, g.seed, weak, getattr(g, "name", ""))
+    def graph(self, g, weak=None, modules=None):
+        """Upload a workloads.Graph-like object (kinds, params, src, dst, seed).
+        modules: {task: GraphHandle} naming the graph each TG_MODULE task composes."""
+        if modules is None:
+            return self.create(g.kinds, g.params, g.src, g.dst, g.seed, weak, getattr(g, "name", ""))
+        st, h = B.tg_graph_create_composed(self.ctx, g.kinds, g.params, g.src, g.dst,
+                                           {v: gh.handle for v, gh in modules.items()}, g.seed, weak)
+        if st != B.TG_OK:
+            raise B.TgError(st, f"tg_graph_create_composed {getattr(g, 'name', '')}")
+        return GraphHandle(self, h, len(g.kinds), len(g.src), getattr(g, "name", ""))
 
     def instance(self, gh: GraphHandle) -> GraphHandle:
         """Another execution instance of gh (own state, shared packed form)."""

@@ -1,0 +1,143 @@
+"""Module tasks (Composable Tasking) on the device: every graph of a
+composition ends with the composed oracle's outputs, counts and digests,
+bit for bit; misuse is refused."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+from oracle import composed as oc
+from workloads.graphs import COND_LOOP, MODULE, STATIC, from_lists, pack_param
+
+pytestmark = pytest.mark.gpu
+R = 4
+
+
+@pytest.fixture(scope="module")
+def ex():
+    from paper_2004_10908_b300 import Executor
+    e = Executor(arena_bytes=1 << 30)
+    yield e
+    e.close()
+
+
+def _run_composed(ex, graphs, modules, root, order):
+    """Create the graphs bottom-up (`order`), run the root, compare all."""
+    handles = {}
+    for key in order:
+        mods = {v: handles[k] for v, k in modules.get(key, {}).items()}
+        handles[key] = ex.graph(graphs[key], modules=mods if mods else None)
+    st = ex.run(handles[root])
+    ref = oc.run(graphs, modules, root)
+    for key in order:
+        out, cnt, dig, execs = ex.result(handles[key])
+        rst, rout, rcnt, rdig, rexecs = ref[key]
+        if key == root:
+            assert st == rst, (key, st, rst)
+        if rst == oracle.OK:
+            np.testing.assert_array_equal(cnt, rcnt, err_msg=f"{key}: cnt")
+            np.testing.assert_array_equal(out, rout, err_msg=f"{key}: out")
+            np.testing.assert_array_equal(dig, rdig, err_msg=f"{key}: dig")
+            assert execs == rexecs, key
+    return st, handles
+
+
+def _destroy(handles, order):
+    for key in reversed(order):
+        handles[key].destroy()
+
+
+def test_paper_composition_example(ex):
+    tf1 = from_lists("taskflow1", [STATIC, STATIC], pack_param([R, R]), [(0, 1)])
+    tf2 = from_lists("taskflow2", [STATIC, STATIC, MODULE], pack_param([R, R, R]), [(0, 1), (1, 2)])
+    st, h = _run_composed(ex, {"tf1": tf1, "tf2": tf2}, {"tf2": {2: "tf1"}}, "tf2", ["tf1", "tf2"])
+    assert st == 0
+    _destroy(h, ["tf1", "tf2"])
+
+
+@pytest.mark.parametrize("T", [1, 2, 5, 9])
+def test_module_in_a_loop(ex, T):
+    body = w.config2a(seed=7, levels=5, width=70, rounds=6)       # 70 sources: several warp rounds
+    top = from_lists("loop", [STATIC, MODULE, COND_LOOP, STATIC],
+                     [pack_param(R), pack_param(R), pack_param(R, T), pack_param(R)],
+                     [(0, 1), (1, 2), (2, 1), (2, 3)])
+    st, h = _run_composed(ex, {"b": body, "t": top}, {"t": {1: "b"}}, "t", ["b", "t"])
+    assert st == 0
+    _destroy(h, ["b", "t"])
+
+
+def test_nested_repeated_and_conditional_modules(ex):
+    g1 = w.nested_loops(3)
+    g2 = from_lists("g2", [STATIC, MODULE, STATIC], pack_param([R] * 3), [(0, 1), (1, 2)])
+    g3 = from_lists("g3", [STATIC, MODULE, MODULE, STATIC, STATIC], pack_param([R] * 5),
+                    [(0, 1), (1, 2), (2, 3), (0, 4), (4, 3)])
+    graphs = {"g1": g1, "g2": g2, "g3": g3}
+    mods = {"g3": {1: "g2", 2: "g2"}, "g2": {1: "g1"}}
+    for _ in range(3):          # repeated launches start every graph afresh
+        st, h = _run_composed(ex, graphs, mods, "g3", ["g1", "g2", "g3"])
+        assert st == 0
+        _destroy(h, ["g1", "g2", "g3"])
+
+
+def test_concurrent_use_is_a_race_or_a_schedule(ex):
+    """Two module tasks with no order between them compose one graph: the
+    run ends RACE, or (if they did not overlap) with the oracle's result."""
+    g1 = w.do_while(40, 16)
+    top = from_lists("par", [STATIC, MODULE, MODULE, STATIC], pack_param([R] * 4),
+                     [(0, 1), (0, 2), (1, 3), (2, 3)])
+    from paper_2004_10908_b300 import binding as B
+    seen = set()
+    for _ in range(10):
+        h1 = ex.graph(g1)
+        ht = ex.graph(top, modules={1: h1, 2: h1})
+        st = ex.run(ht)
+        seen.add(st)
+        if st == 0:
+            ref = oc.run({"g": g1, "t": top}, {"t": {1: "g", 2: "g"}}, "t")
+            np.testing.assert_array_equal(ex.result(ht)[1], ref["t"][2])
+        else:
+            assert st == B.TG_ERR_RACE
+        ht.destroy()
+        h1.destroy()
+    assert seen <= {0, B.TG_ERR_RACE}
+
+
+def test_errors_inside_a_module_reach_the_caller():
+    from paper_2004_10908_b300 import Executor, binding as B
+    with Executor(arena_bytes=1 << 28, exec_cap=40) as e:
+        loop = w.do_while(50, 1)
+        top = from_lists("top", [STATIC, MODULE, STATIC], pack_param([R] * 3), [(0, 1), (1, 2)])
+        hl = e.graph(loop)
+        ht = e.graph(top, modules={1: hl})
+        assert e.run(ht) == B.TG_ERR_EXEC_LIMIT
+        assert oc.run({"l": loop, "t": top}, {"t": {1: "l"}}, "t", exec_cap=40)["t"][0] == oracle.EXEC_LIMIT
+        # the context stays usable: the composed graph alone, then the composition again
+        assert e.run(hl) == B.TG_ERR_EXEC_LIMIT
+        ht.destroy()
+        hl.destroy()
+
+
+def test_refusals_and_standalone_use(ex):
+    from paper_2004_10908_b300 import binding as B
+    g1 = w.diamond()
+    top = from_lists("top", [STATIC, MODULE], pack_param([R, R]), [(0, 1)])
+    h1 = ex.graph(g1)
+    ht = ex.graph(top, modules={1: h1})
+    assert B.tg_instance_create(ex.ctx, ht.handle)[0] == B.TG_ERR_INVALID
+    st, _ = B.tg_batch_create(ex.ctx, [ht.handle])
+    assert st == B.TG_ERR_INVALID
+    assert ex.capture_run(ht, 2)[0] == B.TG_ERR_INVALID
+    assert B.tg_graph_destroy(ex.ctx, h1.handle) == B.TG_ERR_BUSY        # still composed
+    # module task without a graph, a graph for a static task
+    assert B.tg_graph_create_composed(ex.ctx, top.kinds, top.params, top.src, top.dst, {})[0] == B.TG_ERR_INVALID
+    assert B.tg_graph_create_composed(ex.ctx, top.kinds, top.params, top.src, top.dst,
+                                      {0: h1.handle, 1: h1.handle})[0] == B.TG_ERR_INVALID
+    assert B.tg_graph_create(ex.ctx, top.kinds, top.params, top.src, top.dst)[0] == B.TG_ERR_INVALID
+    # the composed graph runs alone like any graph
+    assert ex.run(ht) == 0
+    assert ex.run(h1) == 0
+    ref = oracle.run(g1)
+    np.testing.assert_array_equal(ex.result(h1)[0], ref.out)
+    ht.destroy()
+    assert B.tg_graph_destroy(ex.ctx, h1.handle) == 0
+    h1.handle = None
