@@ -187,7 +187,7 @@ def critical_path_tasks(g):
     return 2 * int(g.meta["side"]) - 1
 
 
-def headline(ex, graphs, args, torch, B):
+def headline(ex, graphs, args, torch, B, world=1):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = ex.stream
     handles = [ex.graph(g) for g in graphs]
@@ -204,6 +204,7 @@ def headline(ex, graphs, args, torch, B):
     step_ms = []
     with ClockSampler() as clk:
         torch.cuda.synchronize()
+        barrier(world)
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -215,6 +216,7 @@ def headline(ex, graphs, args, torch, B):
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
+        barrier(world)
     # scheduler-kernel time per graph (events around the kernel, same stream)
     per_graph = {}
     for h, g in zip(handles, graphs):
@@ -429,31 +431,62 @@ def serving(Executor, torch):
     return out
 
 
+# ---------------------------------------------------------------------------
+# ranks: N independent replicas (one per GPU), no data-path collective; the
+# timed region is bracketed by barriers and its time is the max over ranks
+# ---------------------------------------------------------------------------
+def rank_world():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def init_ranks(world, backend="nccl"):
+    """One process group over the replicas (NCCL on GPUs, gloo on CPU)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device="cuda"):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank_step, world, ms_per_step):
+    """Units all ranks processed per second, with the slowest rank's time."""
+    return units_per_rank_step * world / (ms_per_step / 1000.0)
+
+
 def run_b300(args):
     import torch
 
     from paper_2004_10908_b300 import Executor
     from paper_2004_10908_b300 import binding as B
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        dist.init_process_group("nccl")
+    rank, world = rank_world()
+    init_ranks(world)
     graphs = _graphs()
     execs_per_step = sum(g.n for g in graphs)   # static DAGs: every task runs once
     peaks, peak_kind = _peaks()
 
     ex = Executor(arena_bytes=(512 << 20) if SMALL else (4 << 30))
-    step_ms, per_graph, clocks, stats = headline(ex, graphs, args, torch, B)
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    step_ms, per_graph, clocks, stats = headline(ex, graphs, args, torch, B, world)
+    tot_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = tot_ms / args.steps
-    value = execs_per_step * world / (ms_per_step / 1000.0)
+    value = whole_job_value(execs_per_step, world, ms_per_step)
 
     # roofline of the dominant kernel (the scheduler): graph-metadata bytes
     # per launch over its average launch time, against the measured HBM copy
@@ -513,16 +546,20 @@ def run_b300(args):
         "gpu_launches": 3 * len(graphs) * args.steps,
         "clocks": clocks,
     }
-    if not SMALL and not args.skip_extras:
+    # the single-GPU comparisons and the CPU baseline: rank 0 only
+    if rank == 0 and not SMALL and not args.skip_extras:
         line["thief_policies"] = thief_policies(Executor)
         line["capturer_baseline"] = capturer_baseline(Executor, torch, B)
-    if not args.skip_batched and not SMALL:
+    if rank == 0 and not args.skip_batched and not SMALL:
         line["batched"] = batched(Executor, torch)
-    if not args.skip_serving and not SMALL:
+    if rank == 0 and not args.skip_serving and not SMALL:
         line["serving"] = serving(Executor, torch)
     if rank == 0:
         line["cpu_baseline"] = _cpu_baseline(graphs)
         print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def main():
