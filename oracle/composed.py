@@ -8,7 +8,8 @@ Semantics, written out (the paper's module task, with the reading this
 project takes where the paper is silent -- the paper's module runs the
 composed taskflow to completion and only then lets the module's successors
 proceed; it says nothing about data, so the module task's own output is what
-flows):
+flows).  Subflow tasks ("Dynamic Tasking", joined -- the default) follow
+after the module rules:
   - a module task computes its payload like a static task (count, digest,
     output), then runs its composed graph to completion: that graph's
     sources are activated with the module task's output as their input sum,
@@ -18,10 +19,17 @@ flows):
     releases its own successors (strong edges) with its output;
   - an error inside a composed graph (race, execution cap) ends the whole
     run with that status;
-  - every graph of the composition starts a run from its initial state.
+  - every graph of the composition starts a run from its initial state;
+  - a subflow task (kind 5) computes its payload, then spawns a fresh copy of
+    its template graph (initial state, every time) whose sources take the
+    task's output as their input sum, runs it to completion, and releases its
+    own successors with its output plus the sum of the outputs of every
+    execution of a static task without successors in that copy (the join
+    value, mod 2^32); copies spawned by different tasks are independent.
 
 graphs: dict key -> workloads.Graph; modules: dict key -> {task: key of the
-graph it composes}; kinds use 4 for a module task.
+graph it composes, or of the template it spawns}; kinds use 4 for a module
+task and 5 for a subflow task.
 """
 from __future__ import annotations
 
@@ -31,7 +39,7 @@ import numpy as np
 
 from . import condition_index, mix32, payload, OK, RACE, EXEC_LIMIT, DEFAULT_EXEC_CAP
 
-STATIC, COND_BRANCH, COND_LOOP, COND_CONST, MODULE = 0, 1, 2, 3, 4
+STATIC, COND_BRANCH, COND_LOOP, COND_CONST, MODULE, SUBFLOW = 0, 1, 2, 3, 4, 5
 
 
 class _Failed(Exception):
@@ -50,7 +58,7 @@ class _State:
         win = [0] * n
         for s, d in zip(g.src.tolist(), g.dst.tolist()):   # insertion order
             self.succ[s].append(d)
-            if self.kinds[s] in (STATIC, MODULE):
+            if self.kinds[s] in (STATIC, MODULE, SUBFLOW):
                 self.sin[d] += 1
             else:
                 win[d] += 1
@@ -74,8 +82,10 @@ def run(graphs, modules, root, exec_cap=DEFAULT_EXEC_CAP):
             states[key] = _State(graphs[key])
         return states[key]
 
-    def run_graph(key, source_insum):
-        st = state(key)
+    def run_graph(key, source_insum, st=None):
+        """Run a graph to completion; returns the sum of its sink outputs."""
+        st = st or state(key)
+        sink_sum = 0
         q = deque()
 
         def push(v, s):
@@ -98,6 +108,8 @@ def run(graphs, modules, root, exec_cap=DEFAULT_EXEC_CAP):
             if st.execs > exec_cap:
                 raise _Failed(EXEC_LIMIT)
             kind = st.kinds[v]
+            if kind == STATIC and not st.succ[v]:
+                sink_sum = (sink_sum + x) & 0xFFFFFFFF
             if kind in (COND_BRANCH, COND_LOOP, COND_CONST):
                 r = condition_index(kind, st.params[v], int(st.g.seed), v, it, len(st.succ[v]))
                 if 0 <= r < len(st.succ[v]):
@@ -105,6 +117,9 @@ def run(graphs, modules, root, exec_cap=DEFAULT_EXEC_CAP):
                 continue
             if kind == MODULE:
                 run_graph(modules[key][v], x)   # the composed graph runs to completion first
+            elif kind == SUBFLOW:
+                tmpl = modules[key][v]         # a fresh copy of the template, joined
+                x = (x + run_graph(tmpl, x, _State(graphs[tmpl]))) & 0xFFFFFFFF
             for u in st.succ[v]:
                 st.w_sum[u] = (st.w_sum[u] + x) & 0xFFFFFFFF
                 st.w_cnt[u] -= 1
@@ -113,6 +128,7 @@ def run(graphs, modules, root, exec_cap=DEFAULT_EXEC_CAP):
                     st.w_cnt[u] = st.sin[u]
                     st.w_sum[u] = 0
                     push(u, s2)
+        return sink_sum
 
     status = OK
     try:

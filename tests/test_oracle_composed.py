@@ -90,3 +90,74 @@ def test_errors_inside_a_module_end_the_run():
     assert oc.run({"r": racy, "t": top}, {"t": {1: "r"}}, "t")["t"][0] == oracle.RACE
     loop = w.do_while(50, 1)
     assert oc.run({"l": loop, "t": top}, {"t": {1: "l"}}, "t", exec_cap=40)["t"][0] == oracle.EXEC_LIMIT
+
+
+def test_paper_subflow_example():
+    """Dynamic Tasking example: A precedes B and C, D succeeds B and C; B
+    spawns B1, B2 -> B3 (joined).  B's successors receive B's output plus
+    the outputs of the subflow's sinks (here B3)."""
+    from workloads.graphs import SUBFLOW
+    sub = from_lists("B_subflow", [STATIC] * 3, pack_param([R] * 3), [(0, 2), (1, 2)])
+    top = from_lists("fig", [STATIC, SUBFLOW, STATIC, STATIC], pack_param([R] * 4),
+                     [(0, 1), (0, 2), (1, 3), (2, 3)])
+    res = oc.run({"s": sub, "t": top}, {"t": {1: "s"}}, "t")
+    st, out, cnt, dig, execs = res["t"]
+    assert st == oracle.OK and list(cnt) == [1, 1, 1, 1]
+    a = oracle.payload(0, 0, 0, R)
+    b = oracle.payload(1, 0, a, R)
+    b1 = oracle.payload(0, 0, b, R)
+    b2 = oracle.payload(1, 0, b, R)
+    b3 = oracle.payload(2, 0, (b1 + b2) & 0xFFFFFFFF, R)
+    c = oracle.payload(2, 0, a, R)
+    d = oracle.payload(3, 0, (b + b3 + c) & 0xFFFFFFFF, R)
+    assert list(out) == [a, b, c, d]
+    assert "s" not in res          # a subflow's copies are internal to their spawning task
+
+
+def test_subflow_in_a_loop_is_fresh_each_time():
+    """I -> S (subflow of a 2-chain) -> C (loop, trip T) -> weak [S, X]: every
+    spawn starts the chain from iteration 0."""
+    from workloads.graphs import SUBFLOW
+    T = 4
+    chain = from_lists("c2", [STATIC, STATIC], pack_param([R, R]), [(0, 1)])
+    top = from_lists("loop", [STATIC, SUBFLOW, COND_LOOP, STATIC],
+                     [pack_param(R), pack_param(R), pack_param(R, T), pack_param(R)],
+                     [(0, 1), (1, 2), (2, 1), (2, 3)])
+    res = oc.run({"c": chain, "t": top}, {"t": {1: "c"}}, "t")
+    st, out, cnt, dig, execs = res["t"]
+    assert st == oracle.OK and list(cnt) == [1, T, T, 1]
+    i_out = oracle.payload(0, 0, 0, R)
+    insum = i_out
+    for k in range(T):
+        s = oracle.payload(1, k, insum, R)
+        c0 = oracle.payload(0, 0, s, R)          # fresh copy: iteration 0 every spawn
+        c1 = oracle.payload(1, 0, c0, R)
+        join = (s + c1) & 0xFFFFFFFF
+        cond = oracle.payload(2, k, join, R)
+        insum = cond                             # weak jump back to S carries C's output
+    x = oracle.payload(3, 0, cond, R)
+    assert out[1] == s and out[2] == cond and out[3] == x
+
+
+def test_parallel_subflows_of_one_template_are_independent():
+    """Two subflow tasks spawning one template get independent fresh copies:
+    the same results as two identical but separate templates, and different
+    from a module (whose one graph keeps its state between entries)."""
+    from workloads.graphs import SUBFLOW
+    tmpl = w.nested_loops(2)
+    twin = w.nested_loops(2)
+    par = from_lists("par", [STATIC, SUBFLOW, SUBFLOW, STATIC], pack_param([R] * 4),
+                     [(0, 1), (0, 2), (1, 3), (2, 3)])
+    shared = oc.run({"n": tmpl, "t": par}, {"t": {1: "n", 2: "n"}}, "t")["t"]
+    separate = oc.run({"n": tmpl, "m": twin, "t": par}, {"t": {1: "n", 2: "m"}}, "t")["t"]
+    assert shared[0] == oracle.OK
+    for a, b in zip(shared[1:4], separate[1:4]):
+        np.testing.assert_array_equal(a, b)
+    seq = from_lists("seq", [STATIC, SUBFLOW, SUBFLOW, STATIC], pack_param([R] * 4),
+                     [(0, 1), (1, 2), (2, 3)])
+    as_sub = oc.run({"n": tmpl, "t": seq}, {"t": {1: "n", 2: "n"}}, "t")["t"]
+    seq_mod = from_lists("seqm", [STATIC, MODULE, MODULE, STATIC], pack_param([R] * 4),
+                         [(0, 1), (1, 2), (2, 3)])
+    as_mod = oc.run({"n": tmpl, "t": seq_mod}, {"t": {1: "n", 2: "n"}}, "t")["t"]
+    assert as_sub[0] == as_mod[0] == oracle.OK
+    assert as_sub[1][3] != as_mod[1][3]    # join values differ from the module's plain output

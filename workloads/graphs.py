@@ -21,7 +21,7 @@ import numpy as np
 
 from .rng import Stream
 
-STATIC, COND_BRANCH, COND_LOOP, COND_CONST, MODULE = 0, 1, 2, 3, 4
+STATIC, COND_BRANCH, COND_LOOP, COND_CONST, MODULE, SUBFLOW = 0, 1, 2, 3, 4, 5
 
 
 def pack_param(rounds, trip=0, const_index=0):
