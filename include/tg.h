@@ -68,8 +68,16 @@ typedef struct tg_batch tg_batch;
  * and only then are the module task's successors released (strong edges)
  * with its output.  Two module tasks must not use one graph at the same
  * time: entering a graph that is in use ends the caller with TG_ERR_RACE;
- * an error inside the composed graph becomes the caller's status. */
-enum { TG_STATIC = 0, TG_COND_BRANCH = 1, TG_COND_LOOP = 2, TG_COND_CONST = 3, TG_MODULE = 4 };
+ * an error inside the composed graph becomes the caller's status.
+ * TG_SUBFLOW (Dynamic Tasking, joined subflow): the task runs its payload,
+ * then spawns a fresh copy of its template graph (every task at its initial
+ * state), whose sources take the task's output as their input sum; when the
+ * copy completes, the task's successors are released with its output plus
+ * the sum (mod 2^32) of the outputs of every execution of a static task
+ * without successors in the copy.  Each subflow task owns one copy, so
+ * subflows of different tasks run concurrently. */
+enum { TG_STATIC = 0, TG_COND_BRANCH = 1, TG_COND_LOOP = 2, TG_COND_CONST = 3, TG_MODULE = 4,
+       TG_SUBFLOW = 5 };
 
 enum {
     TG_OK = 0,
@@ -144,11 +152,16 @@ int tg_ctx_destroy(tg_ctx *ctx);
 int tg_graph_create(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
                     uint32_t n_edges, const uint32_t *src, const uint32_t *dst,
                     const uint8_t *weak, uint32_t seed, tg_graph **out);
-/* As tg_graph_create, with module tasks (Composable Tasking, "composed_of"):
- * modules[n_nodes] names, for every TG_MODULE task, the graph it composes
- * (NULL for every other task).  A composed graph belongs to the same
- * context, is not an instance, and may itself compose others; it cannot be
- * destroyed while a graph composing it exists (TG_ERR_BUSY).  A graph with
+/* As tg_graph_create, with module tasks (Composable Tasking, "composed_of")
+ * and subflow tasks (Dynamic Tasking): modules[n_nodes] names, for every
+ * TG_MODULE task, the graph it composes and, for every TG_SUBFLOW task, the
+ * template of its subflow (NULL for every other task).  A composed graph or
+ * template belongs to the same context and is not an instance; a composed
+ * graph may itself compose others, a template holds neither module nor
+ * subflow tasks.  Each subflow task gets its own copy of its template at
+ * creation (an instance, counted against the memory budget, freed with the
+ * graph).  A graph used this way cannot be destroyed while a graph using it
+ * exists (TG_ERR_BUSY).  A graph with
  * module tasks runs with tg_run / tg_submit: each launch starts every graph
  * it composes (transitively) from its initial state, and afterwards
  * tg_result_copy on a composed graph reads its tasks' results.  Batches,

@@ -13,7 +13,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtg.so")
 
-TG_STATIC, TG_COND_BRANCH, TG_COND_LOOP, TG_COND_CONST, TG_MODULE = 0, 1, 2, 3, 4
+TG_STATIC, TG_COND_BRANCH, TG_COND_LOOP, TG_COND_CONST, TG_MODULE, TG_SUBFLOW = 0, 1, 2, 3, 4, 5
 TG_OK, TG_PENDING = 0, 1
 TG_ERR_INVALID, TG_ERR_NO_SOURCE, TG_ERR_EDGE_KIND, TG_ERR_BUDGET = -1, -2, -3, -4
 TG_ERR_RACE, TG_ERR_EXEC_LIMIT, TG_ERR_TIMEOUT, TG_ERR_CANCELLED = -5, -6, -7, -8

@@ -121,7 +121,8 @@ struct tg_graph {
     cudaGraphExec_t cap_exec = nullptr;   // capturer baseline (Algorithm 1), built for cap_streams
     u32 cap_streams = 0;
     std::vector<tg_graph *> mods;         // graphs its module tasks compose (distinct)
-    u32 n_mod = 0;                        // module tasks
+    std::vector<tg_graph *> sub_insts;    // one copy of its template per subflow task
+    u32 n_mod = 0;                        // module and subflow tasks
     int n_refs = 0;                       // graphs whose module tasks compose this one
 };
 
@@ -570,19 +571,21 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
     // ---- validation (same order as the rule statement in tg.h)
     u32 n_cond = 0, n_mod = 0;
     for (u32 v = 0; v < n; ++v) {
-        if (kinds[v] > TG_MODULE || (kinds[v] == TG_MODULE && !modules))
+        if (kinds[v] > TG_SUBFLOW || (kinds[v] >= TG_MODULE && !modules))
             return TG_ERR_INVALID;
         if (kinds[v] == TG_COND_LOOP && ((params[v] >> 16) & 0xFFu) == 0u)
             return TG_ERR_INVALID;
         if (modules) {
             const tg_graph *mg = modules[v];
-            if ((kinds[v] == TG_MODULE) != (mg != nullptr))
+            if ((kinds[v] >= TG_MODULE) != (mg != nullptr))
                 return TG_ERR_INVALID;
             if (mg && (mg->ctx != c || mg->tmpl != nullptr))
                 return TG_ERR_INVALID;
+            if (mg && kinds[v] == TG_SUBFLOW && mg->n_mod != 0)
+                return TG_ERR_INVALID;   // a template holds no module or subflow tasks
         }
         n_cond += is_cond(kinds[v]);
-        n_mod += kinds[v] == TG_MODULE;
+        n_mod += kinds[v] >= TG_MODULE;
     }
     for (u32 e = 0; e < m; ++e)
         if (src[e] >= n || dst[e] >= n)
@@ -658,12 +661,23 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
         tg_graph_destroy(c, g);
         return rc;
     }
+    if (modules)
+        for (u32 v = 0; v < n; ++v)
+            if (kinds[v] == TG_SUBFLOW) {
+                tg_graph *inst = nullptr;
+                int ri = tg_instance_create(c, modules[v], &inst);
+                if (ri != TG_OK) {
+                    tg_graph_destroy(c, g);
+                    return ri;
+                }
+                g->sub_insts.push_back(inst);
+            }
     cudaStreamSynchronize(c->stream);   // staging buffer may still feed an earlier copy
     u32 *he = (u32 *)c->h_stage;
     NodeSlot *hs = (NodeSlot *)(he + (g->pristine_off - g->edge_off));
     u32 *hc = (u32 *)(c->h_stage + edge_bytes);
     const u32 edge_base = (u32)g->edge_off;
-    u32 acc = 0;
+    u32 acc = 0, sub_i = 0;
     for (u32 v = 0; v < n; ++v) {
         NodeSlot s;
         const u32 kind = kinds[v];
@@ -682,6 +696,8 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
         memcpy(&hs[v], &s, sizeof(s));
         if (kind == TG_MODULE)
             he[acc++] = modules[v]->gid;
+        else if (kind == TG_SUBFLOW)
+            he[acc++] = g->sub_insts[sub_i++]->gid;
         outdeg[v] = acc;   // reuse as the fill cursor
         acc += (u32)(s.deg & 0xFFFFu);
     }
@@ -694,7 +710,7 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
             he[m + n_mod + k++] = v;
     if (modules)
         for (u32 v = 0; v < n; ++v)
-            if (modules[v] && std::find(g->mods.begin(), g->mods.end(), modules[v]) == g->mods.end()) {
+            if (kinds[v] == TG_MODULE && std::find(g->mods.begin(), g->mods.end(), modules[v]) == g->mods.end()) {
                 g->mods.push_back(modules[v]);
                 modules[v]->n_refs++;
             }
@@ -796,6 +812,14 @@ int tg_instance_create(tg_ctx *c, tg_graph *t, tg_graph **out)
     g->n_inst = 0;
     g->busy = nullptr;
     g->ready = nullptr;
+    // what belongs to the template alone stays with it
+    g->n_refs = 0;
+    g->mods.clear();
+    g->sub_insts.clear();
+    g->cap_exec = nullptr;
+    g->cap_streams = 0;
+    g->serve_ticket = 0;
+    g->setup_pending = false;
     g->node_off = g->chunk_off << kChunkShift;
     g->edge_len = 0;   // the packed form stays with the template
     g->bytes = bytes;
@@ -838,6 +862,9 @@ int tg_graph_destroy(tg_ctx *c, tg_graph *g)
         cudaGraphExecDestroy(g->cap_exec);
     for (tg_graph *mg : g->mods)
         mg->n_refs--;
+    for (tg_graph *inst : g->sub_insts)
+        tg_graph_destroy(c, inst);
+    g->sub_insts.clear();
     c->nodes.release(g->chunk_off, g->n_chunks);
     if (g->edge_len)
         c->edge_pool.release(g->edge_off, g->edge_len);
@@ -901,6 +928,7 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     if (g->n_mod) {
         // every graph the composition reaches starts idle from its initial state
         std::vector<tg_graph *> todo(g->mods.begin(), g->mods.end()), seen;
+        todo.insert(todo.end(), g->sub_insts.begin(), g->sub_insts.end());
         while (!todo.empty()) {
             tg_graph *mg = todo.back();
             todo.pop_back();
@@ -908,6 +936,7 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
                 continue;
             seen.push_back(mg);
             todo.insert(todo.end(), mg->mods.begin(), mg->mods.end());
+            todo.insert(todo.end(), mg->sub_insts.begin(), mg->sub_insts.end());
         }
         p.has_modules = 1u;
         for (tg_graph *mg : seen) {

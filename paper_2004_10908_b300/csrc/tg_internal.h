@@ -36,7 +36,8 @@ struct alignas(64) GDesc {
     u32 n_src;
     u32 exec_cap;
     u32 ret;        // composed graph in use: the module task to resume when it completes (else kEmpty32)
-    u32 pad[6];
+    u32 acc;        // subflow copy: sum of its sink outputs in the current spawn
+    u32 pad[5];
 };
 static_assert(sizeof(GDesc) == 64, "GDesc is 64 bytes");
 

@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
             }
         }
         // a module task's list starts with the slot id of the graph it composes
-        const u32 succ_off = imm.x + ((modules && ((imm.z >> 16) & 0xFFu) == TG_MODULE) ? 1u : 0u);
+        const u32 succ_off = imm.x + ((modules && ((imm.z >> 16) & 0xFFu) >= TG_MODULE) ? 1u : 0u);
         const u32 succ_cnt = imm.y & 0xFFFFu;
         const u32 indeg = imm.y >> 16;
         const u32 rounds = imm.z & 0xFFFFu;
@@ -759,8 +759,8 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
         const u32 lid = imm.w;
         const u32 iter = stt.x & ~(kInflight | kAwait);
         // a module task whose composed graph finished: release its successors
-        const bool cont = modules && act && kind == TG_MODULE && (stt.x & kAwait) != 0u;
-        const bool enter = modules && act && kind == TG_MODULE && !cont;
+        const bool cont = modules && act && kind >= TG_MODULE && (stt.x & kAwait) != 0u;
+        const bool enter = modules && act && kind >= TG_MODULE && !cont;
 
         // Successor ids of static tasks are fetched before the payload runs,
         // so their latency hides under it.  If no lane has more than
@@ -834,8 +834,14 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
         if (p.trace && act)
             p.trace[2ull * u] = globaltimer();
         // ---- payload
-        const u32 x = cont ? __ldcg(&p.outv[u]) : (act ? task_payload(lid, iter, insum, rounds) : 0u);
+        const u32 x = cont ? __ldcg(&p.outv[u]) +
+                                 (kind == TG_SUBFLOW ? vld32(&p.descs[ld_imm<kServe>(&p.edges[imm.x])].acc) : 0u)
+                           : (act ? task_payload(lid, iter, insum, rounds) : 0u);
         const u32 dg = cont ? stt.y : mix32(stt.y ^ x);
+        // a static sink of a subflow copy adds its output to the copy's join value
+        const bool sink_acc = modules && act && c_status == 0 && kind == TG_STATIC && succ_cnt == 0u;
+        if (sink_acc)
+            atomicAdd(&p.descs[gid].acc, x);
         if (traced) {
             asm volatile("" ::"r"(dg));
             mark(2);
@@ -1035,7 +1041,7 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
         // the next step that does.  The server always fences: the host reads
         // its completion records while it runs.  A module task keeps its flag
         // (and marks itself waiting) until its continuation has run.
-        const bool any_enter = modules && __any_sync(kFull, enter && run);
+        const bool any_enter = modules && __any_sync(kFull, (enter && run) || sink_acc);
         if (race_check) {
             if (run)
                 __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt),
@@ -1056,19 +1062,41 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
             // a fence -- activates the graph's sources with its output.  A
             // refused entry resumes at once.
             bool entered = false;
-            u32 m_base = 0, m_src = 0, m_nsrc = 0;
+            u32 m_base = 0, m_src = 0, m_nsrc = 0, m_n = 0, m_g = 0;
             if (enter && run) {
-                const u32 mg = ld_imm<kServe>(&p.edges[imm.x]);
-                m_nsrc = ld_imm<kServe>(&p.descs[mg].n_src);
-                m_src = ld_imm<kServe>(&p.descs[mg].src_off);
-                m_base = ld_imm<kServe>(&p.descs[mg].node_off);
-                const u64 was = atomicAdd(&p.descs[mg].pe, (u64)m_nsrc);
+                m_g = ld_imm<kServe>(&p.edges[imm.x]);
+                m_nsrc = ld_imm<kServe>(&p.descs[m_g].n_src);
+                m_src = ld_imm<kServe>(&p.descs[m_g].src_off);
+                m_base = ld_imm<kServe>(&p.descs[m_g].node_off);
+                m_n = ld_imm<kServe>(&p.descs[m_g].n);
+                const u64 was = atomicAdd(&p.descs[m_g].pe, (u64)m_nsrc);
                 if ((u32)was == 0u) {
-                    vst32(&p.descs[mg].ret, u);
+                    vst32(&p.descs[m_g].ret, u);
+                    if (kind == TG_SUBFLOW) {
+                        // a fresh copy: no executions, no status, no join value yet
+                        vst64(&p.descs[m_g].pe, (u64)m_nsrc);
+                        vst32((u32 *)&p.descs[m_g].status, 0u);
+                        vst32(&p.descs[m_g].acc, 0u);
+                    }
                     entered = true;
                 } else {
-                    atomicAdd(&p.descs[mg].pe, (u64)0 - (u64)m_nsrc);
+                    atomicAdd(&p.descs[m_g].pe, (u64)0 - (u64)m_nsrc);
                     atomicCAS(&p.descs[gid].status, 0, TG_ERR_RACE);
+                }
+            }
+            // a subflow copy's tasks start from their initial state
+            {
+                u32 rs = __ballot_sync(kFull, entered && kind == TG_SUBFLOW);
+                while (rs) {
+                    const int l = __ffs(rs) - 1;
+                    rs &= rs - 1u;
+                    const u32 nb = __shfl_sync(kFull, m_base, l);
+                    const u32 nn = __shfl_sync(kFull, m_n, l);
+                    for (u32 i = (u32)lane; i < nn; i += 32u) {
+                        NodeSlot *sl = &p.slots[nb + i];
+                        vst64(&sl->W, (u64)(ld_imm<kServe>(&sl->deg) >> 16));
+                        vst64(reinterpret_cast<u64 *>(&sl->cnt), 0ull);
+                    }
                 }
             }
             fence_acq_rel_gpu();
@@ -1262,6 +1290,7 @@ __global__ void module_rearm_kernel(KParams p, u32 gid, u32 n)
         D.pe = 0ull;
         D.status = 0;
         D.ret = kEmpty32;
+        D.acc = 0u;
     }
 }
 

@@ -47,3 +47,20 @@ def test_capture_refuses_conditions_and_bad_stream_counts(ex):
     assert ex.capture_run(gh, 0)[0] == B.TG_ERR_INVALID
     assert ex.capture_run(gh, 33)[0] == B.TG_ERR_INVALID
     gh.destroy()
+
+
+def test_instances_do_not_share_the_templates_capture(ex):
+    """An instance made after its template was captured has its own capture;
+    destroying the instance leaves the template's intact."""
+    from paper_2004_10908_b300 import binding as B
+    g = w.diamond()
+    ref = oracle.run(g)
+    gh = ex.graph(g)
+    assert ex.capture_run(gh, 2)[0] == 0
+    inst = ex.instance(gh)
+    assert ex.capture_run(inst, 2)[0] == 0
+    inst.destroy()
+    st, _ = ex.capture_run(gh, 2)
+    assert st == 0
+    assert_same((st,) + tuple(ex.result(gh)), ref, "template after instance")
+    gh.destroy()

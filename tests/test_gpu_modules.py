@@ -1,13 +1,13 @@
-"""Module tasks (Composable Tasking) on the device: every graph of a
-composition ends with the composed oracle's outputs, counts and digests,
-bit for bit; misuse is refused."""
+"""Module tasks (Composable Tasking) and joined subflows (Dynamic Tasking) on
+the device: every graph of a composition ends with the composed oracle's
+outputs, counts and digests, bit for bit; misuse is refused."""
 import numpy as np
 import pytest
 
 import oracle
 import workloads as w
 from oracle import composed as oc
-from workloads.graphs import COND_LOOP, MODULE, STATIC, from_lists, pack_param
+from workloads.graphs import COND_LOOP, MODULE, STATIC, SUBFLOW, from_lists, pack_param
 
 pytestmark = pytest.mark.gpu
 R = 4
@@ -30,6 +30,8 @@ def _run_composed(ex, graphs, modules, root, order):
     st = ex.run(handles[root])
     ref = oc.run(graphs, modules, root)
     for key in order:
+        if key not in ref:
+            continue        # a subflow template: its copies are internal to their tasks
         out, cnt, dig, execs = ex.result(handles[key])
         rst, rout, rcnt, rdig, rexecs = ref[key]
         if key == root:
@@ -141,3 +143,58 @@ def test_refusals_and_standalone_use(ex):
     ht.destroy()
     assert B.tg_graph_destroy(ex.ctx, h1.handle) == 0
     h1.handle = None
+
+
+def test_paper_subflow_example(ex):
+    sub = from_lists("B_subflow", [STATIC] * 3, pack_param([R] * 3), [(0, 2), (1, 2)])
+    top = from_lists("fig", [STATIC, SUBFLOW, STATIC, STATIC], pack_param([R] * 4),
+                     [(0, 1), (0, 2), (1, 3), (2, 3)])
+    st, h = _run_composed(ex, {"s": sub, "t": top}, {"t": {1: "s"}}, "t", ["s", "t"])
+    assert st == 0
+    _destroy(h, ["s", "t"])
+
+
+@pytest.mark.parametrize("T", [1, 3, 7])
+def test_subflow_in_a_loop(ex, T):
+    tmpl = w.config2a(seed=11, levels=4, width=50, rounds=5)       # 50 sources, many sinks
+    top = from_lists("loop", [STATIC, SUBFLOW, COND_LOOP, STATIC],
+                     [pack_param(R), pack_param(R), pack_param(R, T), pack_param(R)],
+                     [(0, 1), (1, 2), (2, 1), (2, 3)])
+    st, h = _run_composed(ex, {"s": tmpl, "t": top}, {"t": {1: "s"}}, "t", ["s", "t"])
+    assert st == 0
+    _destroy(h, ["s", "t"])
+
+
+def test_parallel_subflows_modules_and_conditional_templates(ex):
+    """Four subflow tasks (two templates, one with nested loops) run side by
+    side with a module task; repeated launches start afresh."""
+    loops = w.nested_loops(4)
+    dag = w.config2a(seed=12, levels=3, width=40, rounds=3)
+    modg = w.diamond(R)
+    top = from_lists("mix", [STATIC, SUBFLOW, SUBFLOW, SUBFLOW, SUBFLOW, MODULE, STATIC],
+                     pack_param([R] * 7),
+                     [(0, 1), (0, 2), (0, 3), (0, 4), (0, 5), (1, 6), (2, 6), (3, 6), (4, 6), (5, 6)])
+    graphs = {"loops": loops, "dag": dag, "mod": modg, "t": top}
+    mods = {"t": {1: "loops", 2: "loops", 3: "dag", 4: "dag", 5: "mod"}}
+    for _ in range(3):
+        st, h = _run_composed(ex, graphs, mods, "t", ["loops", "dag", "mod", "t"])
+        assert st == 0
+        _destroy(h, ["loops", "dag", "mod", "t"])
+
+
+def test_subflow_refusals(ex):
+    from paper_2004_10908_b300 import binding as B
+    inner = w.diamond()
+    hi = ex.graph(inner)
+    comp = ex.graph(from_lists("c", [STATIC, MODULE], pack_param([R, R]), [(0, 1)]), modules={1: hi})
+    top = from_lists("t", [STATIC, SUBFLOW], pack_param([R, R]), [(0, 1)])
+    # a template holds no module or subflow tasks
+    assert B.tg_graph_create_composed(ex.ctx, top.kinds, top.params, top.src, top.dst,
+                                      {1: comp.handle})[0] == B.TG_ERR_INVALID
+    ht = ex.graph(top, modules={1: hi})
+    assert B.tg_graph_destroy(ex.ctx, hi.handle) == B.TG_ERR_BUSY      # its copy exists
+    assert ex.run(ht) == 0
+    ht.destroy()
+    comp.destroy()
+    assert B.tg_graph_destroy(ex.ctx, hi.handle) == 0
+    hi.handle = None
