@@ -329,6 +329,78 @@ def oracle_all_cores(graphs, what):
             "sample": f"{what}: {len(graphs)} graphs, {execs} executions, {dt:.2f} s"}
 
 
+def composition(Executor, torch):
+    """Module tasks and joined subflows in one launch, against the host
+    re-launching the same graphs: a module task entered 50 times in a loop
+    (composed graph: layered 10 x 100, in-degree 1-4, 16 rounds), and 64
+    subflow tasks side by side, each spawning a copy of that graph.  Root
+    results are checked against the composed oracle."""
+    from oracle import composed as oc
+    from workloads.graphs import COND_LOOP, MODULE, STATIC, SUBFLOW, from_lists, pack_param
+    body = w.config2a(seed=21, levels=10, width=100, d_lo=1, d_hi=4, rounds=16)
+    T, K, R = 50, 64, 16
+    loop = from_lists("module_loop", [STATIC, MODULE, COND_LOOP, STATIC],
+                      [pack_param(R), pack_param(R), pack_param(R, T), pack_param(R)],
+                      [(0, 1), (1, 2), (2, 1), (2, 3)])
+    fan = from_lists("subflow_fan", [STATIC] + [SUBFLOW] * K + [STATIC], pack_param([R] * (K + 2)),
+                     [(0, 1 + k) for k in range(K)] + [(1 + k, K + 1) for k in range(K)])
+    out = {"composed_graph": "layered 10 x 100, in-degree 1-4, 16 rounds (1,000 tasks)"}
+    with Executor(arena_bytes=2 << 30) as ex:
+        hb = ex.graph(body)
+
+        def dev_ms(fn):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(ex.stream)
+            fn()
+            e1.record(ex.stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1)
+
+        def run_on_stream(h):
+            st, t = B_submit(ex, h)
+            assert st == 0
+            return t
+
+        for name, top, mods, n_exec in (("module_loop", loop, {1: hb}, T * body.n + 2 * T + 2),
+                                        ("subflow_fan", fan, {k + 1: hb for k in range(K)}, K * body.n + K + 2)):
+            ht = ex.graph(top, modules=mods)
+            ts = []
+            for _ in range(4):
+                tickets = []
+                ts.append(dev_ms(lambda: tickets.append(run_on_stream(ht))))
+                assert ex.wait(tickets[0]) == 0
+            ref = oc.run({"b": body, "t": top}, {"t": {v: "b" for v in mods}}, "t")["t"]
+            got = ex.result(ht)
+            assert ref[0] == 0 and (np.asarray(got[0]) == ref[1]).all() and (np.asarray(got[1]) == ref[2]).all()
+            reps = T if name == "module_loop" else K
+            # wall clock, both ways: one composed run vs the host running the
+            # composed graph `reps` times (launch + wait each)
+            wall = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                assert ex.run(ht) == 0
+                wall.append((time.perf_counter() - t0) * 1e3)
+            plain = []
+            for _ in range(2):
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    assert ex.run(hb) == 0
+                plain.append((time.perf_counter() - t0) * 1e3)
+            ms = statistics.median(ts[1:])
+            out[name] = {"entries": reps, "executions": n_exec, "composed_device_ms": ms,
+                         "tasks_s": n_exec / (ms / 1000.0), "composed_wall_ms": min(wall),
+                         "host_relaunch_wall_ms": min(plain), "relaunch_over_composed": min(plain) / min(wall)}
+            ht.destroy()
+        hb.destroy()
+    return out
+
+
+def B_submit(ex, h):
+    from paper_2004_10908_b300 import binding as B
+    return B.tg_submit(ex.ctx, h.handle)
+
+
 def batched(Executor, torch):
     """4,096 graphs in one autotuned, CUDA-graph-captured launch vs one launch each."""
     t0 = time.time()
@@ -550,6 +622,7 @@ def run_b300(args):
     if rank == 0 and not SMALL and not args.skip_extras:
         line["thief_policies"] = thief_policies(Executor)
         line["capturer_baseline"] = capturer_baseline(Executor, torch, B)
+        line["composition"] = composition(Executor, torch)
     if rank == 0 and not args.skip_batched and not SMALL:
         line["batched"] = batched(Executor, torch)
     if rank == 0 and not args.skip_serving and not SMALL:
