@@ -45,6 +45,8 @@ METRIC = "tasks/s and ns/task overhead, batched vs plain per-graph; serving p50/
 UNIT = "tasks/s"
 WORKLOAD = "large static DAGs, plain form: layered 1000x1000 (d~U{1..8}, R=16) + wavefront 1024x1024 (R=256)"
 SMALL = False   # --small: the same two shapes at reduced size (for profiler captures)
+# launch geometries the headline graphs' autotuning picked, for this process only
+TUNE_CACHE = os.path.join(__import__("tempfile").gettempdir(), f"tg_tune_{os.getpid()}.txt")
 
 
 def log(*a):
@@ -191,6 +193,14 @@ def headline(ex, graphs, args, torch, B, world=1):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = ex.stream
     handles = [ex.graph(g) for g in graphs]
+    # each graph keeps the launch geometry its own autotuning picks (untimed)
+    tuned = {}
+    t0 = time.perf_counter()
+    for h, g in zip(handles, graphs):
+        chosen, _ = ex.autotune(h, trials=2, cache_path=TUNE_CACHE)
+        tuned[g.name] = {k: chosen[k] for k in ("worker_blocks", "warps_per_block", "batch_max", "local_keep",
+                                                "max_thieves", "thief_mode", "steal_policy", "max_steal")}
+    tuned["autotune_s"] = time.perf_counter() - t0
 
     def step():
         for h in handles:
@@ -232,10 +242,12 @@ def headline(ex, graphs, args, torch, B, world=1):
     stats = ex.stats()
     for h in handles:
         h.destroy()
-    return step_ms, per_graph, clk.summary(), stats
+    return step_ms, per_graph, clk.summary(), stats, tuned
 
 
 def e2e(ex, graphs, reps):
+    """The user's path: create (ingest, pack, upload), take the tuned
+    geometry from the tuning cache (no runs), run, read every result back."""
     ms = []
     h2d = d2h = 0
     for _ in range(reps):
@@ -243,6 +255,7 @@ def e2e(ex, graphs, reps):
         h2d = d2h = 0
         for g in graphs:
             gh = ex.graph(g)
+            ex.autotune(gh, cache_path=TUNE_CACHE)
             assert ex.run(gh) == 0
             ex.result(gh)
             # copied per graph: successor lists + sources + record image, chunk
@@ -555,7 +568,7 @@ def run_b300(args):
     peaks, peak_kind = _peaks()
 
     ex = Executor(arena_bytes=(512 << 20) if SMALL else (4 << 30))
-    step_ms, per_graph, clocks, stats = headline(ex, graphs, args, torch, B, world)
+    step_ms, per_graph, clocks, stats, tuned = headline(ex, graphs, args, torch, B, world)
     tot_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = tot_ms / args.steps
     value = whole_job_value(execs_per_step, world, ms_per_step)
@@ -596,8 +609,7 @@ def run_b300(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "graphs": [g.name for g in graphs], "tasks_per_step": execs_per_step,
-                   "l2": "flushed between steps (512 MB write)", "worker_blocks": stats["worker_blocks"],
-                   "warps_per_block": stats["warps_per_block"]},
+                   "l2": "flushed between steps (512 MB write)", "launch_geometry": tuned},
         "e2e": {"value": execs_per_step / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks.get("hbm_gbs", 6400.0),

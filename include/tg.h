@@ -266,6 +266,18 @@ int tg_batch_destroy(tg_ctx *ctx, tg_batch *b);
 int tg_batch_autotune(tg_ctx *ctx, tg_batch *b, uint32_t trials, const char *cache_path,
                       tg_ctx_opts *chosen, uint64_t *best_ns);
 
+/* Autotune one graph's launch geometry (the batch knobs above plus
+ * activations per step, local backlog and thief mode) by timing real runs
+ * of it: `trials` timed runs per candidate after one warm-up, coordinate
+ * descent, the winner cached under the device and graph shape in
+ * cache_path (NULL: no cache).  The graph keeps the chosen geometry for its
+ * later tg_run / tg_submit launches.  *chosen / *best_ns (may be NULL)
+ * receive it and its best device time.  Runs the graph several times: its
+ * results afterwards are those of its last run.  TG_ERR_BUSY while serving;
+ * a run's error status ends the search and is returned. */
+int tg_graph_autotune(tg_ctx *ctx, tg_graph *g, uint32_t trials, const char *cache_path, tg_ctx_opts *chosen,
+                      uint64_t *best_ns);
+
 /* Convenience: create, launch, wait and destroy; statuses may be NULL.
  * Returns TG_OK if every graph ended TG_OK, else the first error. */
 int tg_run_batch(tg_ctx *ctx, tg_graph *const *gs, uint32_t n, int *statuses);

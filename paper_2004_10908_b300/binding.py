@@ -76,6 +76,8 @@ SIGNATURES = {
                                      ctypes.POINTER(_vp)]),
     "tg_ctx_destroy": (ctypes.c_int, [_vp]),
     "tg_graph_create": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, ctypes.POINTER(_vp)]),
+    "tg_graph_autotune": (ctypes.c_int, [_vp, _vp, _u32, ctypes.c_char_p, ctypes.POINTER(tg_ctx_opts),
+                                         ctypes.POINTER(_u64)]),
     "tg_graph_create_composed": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, _vp,
                                                 ctypes.POINTER(_vp)]),
     "tg_graph_destroy": (ctypes.c_int, [_vp, _vp]),
@@ -313,6 +315,15 @@ def tg_batch_autotune(ctx, b, trials=2, cache_path=None):
     o = tg_ctx_opts()
     t = _u64(0)
     st = load().tg_batch_autotune(_vp(ctx), _vp(b), trials, cache_path.encode() if cache_path else None,
+                                  ctypes.byref(o), ctypes.byref(t))
+    return st, {k: getattr(o, k) for k, _ in o._fields_}, t.value
+
+
+def tg_graph_autotune(ctx, g, trials=2, cache_path=None):
+    """Returns (status, chosen options dict, best device ns)."""
+    o = tg_ctx_opts()
+    t = _u64(0)
+    st = load().tg_graph_autotune(_vp(ctx), _vp(g), trials, cache_path.encode() if cache_path else None,
                                   ctypes.byref(o), ctypes.byref(t))
     return st, {k: getattr(o, k) for k, _ in o._fields_}, t.value
 

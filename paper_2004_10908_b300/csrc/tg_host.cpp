@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <functional>
 #include <map>
 #include <new>
 #include <vector>
@@ -122,6 +123,8 @@ struct tg_graph {
     u32 cap_streams = 0;
     std::vector<tg_graph *> mods;         // graphs its module tasks compose (distinct)
     std::vector<tg_graph *> sub_insts;    // one copy of its template per subflow task
+    Geometry geo;                         // launch geometry chosen for it (tg_graph_autotune)
+    bool has_geo = false;
     u32 n_mod = 0;                        // module and subflow tasks
     int n_refs = 0;                       // graphs whose module tasks compose this one
 };
@@ -919,7 +922,9 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     }
     if (g->ready)
         TG_CUDA(cudaStreamWaitEvent(c->stream, g->ready, 0));
-    KParams p = base_params(c, c->geo);
+    // the graph's own tuned geometry, else the context's
+    const Geometry &geo = g->has_geo ? g->geo : c->geo;
+    KParams p = base_params(c, geo);
     p.lt = nullptr;
     p.n_graphs = 1;
     p.single_gid = g->gid;
@@ -950,11 +955,11 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     TG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
     TG_CUDA(launch_rearm(p, c->stream));
     TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
-    TG_CUDA(launch_sched(p, c->geo.blocks, c->geo.threads, c->stream));
+    TG_CUDA(launch_sched(p, geo.blocks, geo.threads, c->stream));
     TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
     TG_CUDA(launch_finalize(p, c->stream));
     TG_CUDA(cudaEventRecord(s.ev, c->stream));
-    c->last_geo = c->geo;
+    c->last_geo = geo;
     c->timed = true;
     g->busy = s.ev;
     *ticket = c->next_ticket++;
@@ -1521,23 +1526,16 @@ static std::string batch_key(tg_ctx *c, tg_batch *b)
     return k;
 }
 
-extern "C" {
-
-int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache_path, tg_ctx_opts *chosen,
-                      uint64_t *best_ns)
+// Coordinate descent over the launch knobs; `measure` times one candidate
+// (TG_ERR_INVALID / TG_ERR_CUDA from it skip the candidate, other errors end
+// the search).  A text file caches the winner under `key`.
+static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_path, tg_ctx_opts &best,
+                         u64 &best_t, const std::function<int(const tg_ctx_opts &, u64 &)> &measure)
 {
-    if (!c || !b || b->ctx != c)
-        return TG_ERR_INVALID;
-    if (trials == 0)
-        trials = 2;
-    const std::string key = batch_key(c, b);
-    tg_ctx_opts best{};
-    geometry_to_opts(b->geo, best);
-    u64 best_t = 0;
-    bool cached = false;
     if (cache_path) {
         if (FILE *f = std::fopen(cache_path, "r")) {
             char line[1024];
+            bool hit = false;
             while (std::fgets(line, sizeof(line), f)) {
                 char *tab = std::strchr(line, '\t');
                 if (!tab || std::string(line, tab) != key)
@@ -1552,14 +1550,98 @@ int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache
                     if (resolve_geometry(c, o, g) == TG_OK) {
                         best = o;
                         best_t = t;
-                        cached = true;
+                        hit = true;
                     }
                 }
             }
             std::fclose(f);
+            if (hit)
+                return TG_OK;
         }
     }
-    int status = TG_OK;
+    int rc = measure(best, best_t);
+    if (rc != TG_OK)
+        return rc;
+    const int warps_c[] = {4, 8, 16};
+    const int bpsm_c[] = {1, 2, 4};
+    const int depth_c[] = {(int)std::max<u32>(64u, c->dq_cap / 4u), (int)c->dq_cap};
+    const int policy_c[] = {0, 1};
+    const int steal_c[] = {2, 8, 32};
+    const int thief_c[] = {8, 16, 64};
+    const int batch_c[] = {8, 16, 32};
+    const int keep_c[] = {16, 32, 128, 512};
+    const int tmode_c[] = {0, 1};
+    auto try_knob = [&](auto setter, const int *vals, int nv) -> int {
+        for (int i = 0; i < nv; ++i) {
+            tg_ctx_opts o = best;
+            setter(o, vals[i]);
+            Geometry g;
+            if (resolve_geometry(c, o, g) != TG_OK)
+                continue;
+            geometry_to_opts(g, o);
+            if (std::memcmp(&o, &best, sizeof(o)) == 0)
+                continue;
+            u64 t = 0;
+            int rc2 = measure(o, t);
+            if (rc2 == TG_ERR_INVALID || rc2 == TG_ERR_CUDA)
+                continue;
+            if (rc2 != TG_OK)
+                return rc2;
+            if (t && t < best_t) {
+                best_t = t;
+                best = o;
+            }
+        }
+        return TG_OK;
+    };
+    if ((rc = try_knob([](tg_ctx_opts &o, int v) { o.warps_per_block = v; o.worker_blocks = 0; }, warps_c, 3)) != TG_OK ||
+        (rc = try_knob([&](tg_ctx_opts &o, int v) { o.worker_blocks = v * c->sm_count; }, bpsm_c, 3)) != TG_OK ||
+        (rc = try_knob([](tg_ctx_opts &o, int v) { o.deque_depth = v; }, depth_c, 2)) != TG_OK ||
+        (rc = try_knob([](tg_ctx_opts &o, int v) { o.steal_policy = v; }, policy_c, 2)) != TG_OK ||
+        (rc = try_knob([](tg_ctx_opts &o, int v) { o.max_steal = v; }, steal_c, 3)) != TG_OK ||
+        (rc = try_knob([](tg_ctx_opts &o, int v) { o.max_thieves = v; }, thief_c, 3)) != TG_OK ||
+        (rc = try_knob([](tg_ctx_opts &o, int v) { o.batch_max = v; }, batch_c, 3)) != TG_OK ||
+        (rc = try_knob([](tg_ctx_opts &o, int v) { o.local_keep = v; }, keep_c, 4)) != TG_OK ||
+        (rc = try_knob([](tg_ctx_opts &o, int v) { o.thief_mode = v; }, tmode_c, 2)) != TG_OK)
+        return rc;
+    if (cache_path) {
+        if (FILE *f = std::fopen(cache_path, "a")) {
+            std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %d %d %d %llu\n", key.c_str(), best.worker_blocks,
+                         best.warps_per_block, best.deque_depth, best.steal_policy, best.max_steal,
+                         best.max_thieves, best.smem_ring, best.idle_sleep_ns, best.batch_max, best.local_keep,
+                         best.thief_mode, (unsigned long long)best_t);
+            std::fclose(f);
+        }
+    }
+    return TG_OK;
+}
+
+static std::string graph_key(tg_ctx *c, tg_graph *g)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, c->device);
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s|sm%d|flags%u|graph|n%u|m%u|s%u|c%u|mod%u", prop.name, c->sm_count,
+                  c->opts.flags, g->n, g->m, g->n_src, g->n_cond, g->n_mod);
+    std::string k(buf);
+    for (char &ch : k)
+        if (ch == '\t' || ch == '\n')
+            ch = ' ';
+    return k;
+}
+
+extern "C" {
+
+int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache_path, tg_ctx_opts *chosen,
+                      uint64_t *best_ns)
+{
+    if (!c || !b || b->ctx != c)
+        return TG_ERR_INVALID;
+    if (trials == 0)
+        trials = 2;
+    tg_ctx_opts best{};
+    geometry_to_opts(b->geo, best);
+    u64 best_t = 0;
     auto measure = [&](const tg_ctx_opts &o, u64 &t_out) -> int {
         Geometry g;
         int rc = resolve_geometry(c, o, g);
@@ -1584,75 +1666,86 @@ int tg_batch_autotune(tg_ctx *c, tg_batch *b, uint32_t trials, const char *cache
         t_out = tmin;
         return TG_OK;
     };
-    if (!cached) {
-        int rc = measure(best, best_t);
-        if (rc != TG_OK)
-            return rc;
-        const int warps_c[] = {4, 8, 16};
-        const int bpsm_c[] = {1, 2, 4};
-        const int depth_c[] = {(int)std::max<u32>(64u, c->dq_cap / 4u), (int)c->dq_cap};
-        const int policy_c[] = {0, 1};
-        const int steal_c[] = {2, 8, 32};
-        const int thief_c[] = {8, 16, 64};
-        const int batch_c[] = {8, 16, 32};
-        const int keep_c[] = {16, 32, 128, 512};
-        const int tmode_c[] = {0, 1};
-        auto try_knob = [&](auto setter, const int *vals, int nv) -> int {
-            for (int i = 0; i < nv; ++i) {
-                tg_ctx_opts o = best;
-                setter(o, vals[i]);
-                Geometry g;
-                if (resolve_geometry(c, o, g) != TG_OK)
-                    continue;
-                geometry_to_opts(g, o);
-                if (std::memcmp(&o, &best, sizeof(o)) == 0)
-                    continue;
-                u64 t = 0;
-                int rc = measure(o, t);
-                if (rc == TG_ERR_INVALID || rc == TG_ERR_CUDA)
-                    continue;
-                if (rc != TG_OK)
-                    return rc;
-                if (t && t < best_t) {
-                    best_t = t;
-                    best = o;
-                }
-            }
-            return TG_OK;
-        };
-        int rc2 = TG_OK;
-        if ((rc2 = try_knob([](tg_ctx_opts &o, int v) { o.warps_per_block = v; o.worker_blocks = 0; }, warps_c, 3)) != TG_OK ||
-            (rc2 = try_knob([&](tg_ctx_opts &o, int v) { o.worker_blocks = v * c->sm_count; }, bpsm_c, 3)) != TG_OK ||
-            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.deque_depth = v; }, depth_c, 2)) != TG_OK ||
-            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.steal_policy = v; }, policy_c, 2)) != TG_OK ||
-            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.max_steal = v; }, steal_c, 3)) != TG_OK ||
-            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.max_thieves = v; }, thief_c, 3)) != TG_OK ||
-            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.batch_max = v; }, batch_c, 3)) != TG_OK ||
-            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.local_keep = v; }, keep_c, 4)) != TG_OK ||
-            (rc2 = try_knob([](tg_ctx_opts &o, int v) { o.thief_mode = v; }, tmode_c, 2)) != TG_OK)
-            return rc2;
-        if (cache_path) {
-            if (FILE *f = std::fopen(cache_path, "a")) {
-                std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %d %d %d %llu\n", key.c_str(), best.worker_blocks,
-                             best.warps_per_block, best.deque_depth, best.steal_policy, best.max_steal,
-                             best.max_thieves, best.smem_ring, best.idle_sleep_ns, best.batch_max, best.local_keep,
-                             best.thief_mode, (unsigned long long)best_t);
-                std::fclose(f);
-            }
-        }
-    }
+    int rc = tune_geometry(c, batch_key(c, b), cache_path, best, best_t, measure);
+    if (rc != TG_OK)
+        return rc;
     Geometry g;
-    int rc = resolve_geometry(c, best, g);
+    rc = resolve_geometry(c, best, g);
     if (rc != TG_OK)
         return rc;
     b->geo = g;
     rc = batch_capture(c, b);
     if (rc != TG_OK)
         return rc;
-    (void)status;
     if (chosen) {
         *chosen = c->opts;
         geometry_to_opts(g, *chosen);
+    }
+    if (best_ns)
+        *best_ns = best_t;
+    return TG_OK;
+}
+
+int tg_graph_autotune(tg_ctx *c, tg_graph *g, uint32_t trials, const char *cache_path, tg_ctx_opts *chosen,
+                      uint64_t *best_ns)
+{
+    if (!c || !g || g->ctx != c)
+        return TG_ERR_INVALID;
+    if (c->serving)
+        return TG_ERR_BUSY;
+    if (trials == 0)
+        trials = 2;
+    tg_ctx_opts best{};
+    geometry_to_opts(g->has_geo ? g->geo : c->geo, best);
+    u64 best_t = 0;
+    auto run_once = [&](u64 &ns) -> int {
+        uint64_t t = 0;
+        int rc = tg_submit(c, g, &t);
+        if (rc != TG_OK)
+            return rc;
+        rc = tg_wait(c, t);
+        if (rc != TG_OK)
+            return rc;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1) != cudaSuccess)
+            return TG_ERR_CUDA;
+        ns = (u64)((double)ms * 1e6);
+        return TG_OK;
+    };
+    auto measure = [&](const tg_ctx_opts &o, u64 &t_out) -> int {
+        Geometry geo;
+        int rc = resolve_geometry(c, o, geo);
+        if (rc != TG_OK)
+            return rc;
+        g->geo = geo;
+        g->has_geo = true;
+        u64 t = 0;
+        if ((rc = run_once(t)) != TG_OK)   // warm-up
+            return rc;
+        u64 tmin = 0;
+        for (uint32_t i = 0; i < trials; ++i) {
+            if ((rc = run_once(t)) != TG_OK)
+                return rc;
+            if (t && (tmin == 0 || t < tmin))
+                tmin = t;
+        }
+        t_out = tmin;
+        return TG_OK;
+    };
+    int rc = tune_geometry(c, graph_key(c, g), cache_path, best, best_t, measure);
+    if (rc != TG_OK) {
+        g->has_geo = false;
+        return rc;
+    }
+    Geometry geo;
+    rc = resolve_geometry(c, best, geo);
+    if (rc != TG_OK)
+        return rc;
+    g->geo = geo;
+    g->has_geo = true;
+    if (chosen) {
+        *chosen = c->opts;
+        geometry_to_opts(geo, *chosen);
     }
     if (best_ns)
         *best_ns = best_t;

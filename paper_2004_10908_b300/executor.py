@@ -86,6 +86,13 @@ class Executor:
             raise B.TgError(st, f"tg_graph_create_composed {getattr(g, 'name', '')}")
         return GraphHandle(self, h, len(g.kinds), len(g.src), getattr(g, "name", ""))
 
+    def autotune(self, gh: GraphHandle, trials=2, cache_path=None):
+        """Pick and keep the fastest launch geometry for gh (tg_graph_autotune)."""
+        st, chosen, ns = B.tg_graph_autotune(self.ctx, gh.handle, trials, cache_path)
+        if st != B.TG_OK:
+            raise B.TgError(st, "tg_graph_autotune")
+        return chosen, ns
+
     def instance(self, gh: GraphHandle) -> GraphHandle:
         """Another execution instance of gh (own state, shared packed form)."""
         st, h = B.tg_instance_create(self.ctx, gh.handle)

@@ -145,3 +145,28 @@ def test_full_size_batch_sampled():
         idx = np.random.default_rng(1).choice(len(gs), 64, replace=False)
         _check_against_oracle(ex2, [gs[i] for i in idx], [hs[i] for i in idx], exec_cap=1 << 31)
         b.destroy()
+
+
+def test_graph_autotune_keeps_results_and_caches(tmp_path):
+    """Per-graph autotuning: the chosen geometry is valid, later runs still
+    equal the oracle, and a second call is answered from the cache."""
+    import oracle as orc_mod
+    from paper_2004_10908_b300 import Executor
+    g = w.config1(levels=6, width=60, trip=3, rounds=16)
+    ref = orc_mod.run(g)
+    cache = str(tmp_path / "tune.txt")
+    with Executor(arena_bytes=1 << 30) as e:
+        h = e.graph(g)
+        chosen, ns = e.autotune(h, trials=1, cache_path=cache)
+        assert ns > 0 and 1 <= chosen["warps_per_block"] <= 32 and chosen["worker_blocks"] > 0
+        assert e.run(h) == 0
+        out, cnt, dig, execs = e.result(h)
+        np.testing.assert_array_equal(cnt, ref.cnt)
+        np.testing.assert_array_equal(out, ref.out)
+        np.testing.assert_array_equal(dig, ref.dig)
+        assert e.stats()["warps_per_block"] == chosen["warps_per_block"]
+        lines = open(cache).read().splitlines()
+        assert len(lines) == 1 and "|graph|" in lines[0]
+        chosen2, ns2 = e.autotune(h, trials=1, cache_path=cache)
+        assert chosen2 == chosen and ns2 == ns
+        assert len(open(cache).read().splitlines()) == 1
