@@ -652,13 +652,18 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
                     }
                     if (adaptive) {
                         // the last thief keeps stealing while a block is active or
-                        // a deque advertises work; any other failed thief parks
-                        // its block until a wake ticket (or the end) arrives
+                        // a queue holds work; any other failed thief parks its
+                        // block until a wake ticket (or the end) arrives -- but
+                        // only a block with no busy warp: the thief role is the
+                        // only way into the block's own public deque, which its
+                        // busy warps may still fill
                         const u32 nwa = (p.nblocks + 31u) >> 5;
-                        const int any = __ballot_sync(kFull, (u32)lane < nwa && vld32(&p.ctl->avail[lane]) != 0u) != 0;
+                        const int any = __ballot_sync(kFull, (u32)lane < nwa && vld32(&p.ctl->avail[lane]) != 0u) != 0 ||
+                                        ring_size(w.inj) != 0u;
                         if (lane == 0) {
                             const bool last = atomicSub(&p.ctl->thieves, 1u) == 1u;
-                            if (!stop && !(last && (any || vld32(&p.ctl->actives) != 0u))) {
+                            const bool idle_block = *(volatile u32 *)&s_busy == 0u;
+                            if (!stop && idle_block && !(last && (any || vld32(&p.ctl->actives) != 0u))) {
                                 st_park++;
                                 u32 nap = 256, naps = 0;
                                 for (;;) {
@@ -680,6 +685,10 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
                                     }
                                     const u32 tk = vld32(&p.ctl->wake);
                                     if (tk != 0u && atomicCAS(&p.ctl->wake, tk, tk - 1u) == tk)
+                                        break;
+                                    // a warp of this block that was just starting a
+                                    // step may still publish to the block's deque
+                                    if ((vld32(w.avail_word) & w.avail_bit) != 0u)
                                         break;
                                 }
                                 backoff = 256;

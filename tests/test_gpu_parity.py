@@ -265,3 +265,20 @@ def test_payload_chunking_single_graphs(chunk):
         gh = e.graph(w.do_while(100, 64))
         assert e.run(gh) == B.TG_ERR_EXEC_LIMIT
         gh.destroy()
+
+
+def test_adaptive_thieves_finish_a_wide_wavefront():
+    """Adaptive thieves with a short local backlog on a wide wavefront: busy
+    warps spill to their block's deque while other blocks park; the run must
+    finish (well inside its time limit) with the oracle's results."""
+    from paper_2004_10908_b300 import Executor
+    g = w.config2b(seed=2, side=192, rounds=64)
+    ref = oracle.run(g)
+    for geo in (dict(thief_mode=1, local_keep=16, max_thieves=8), dict(thief_mode=1, local_keep=16, batch_max=8)):
+        with Executor(arena_bytes=1 << 29, time_limit_ns=5_000_000_000, **geo) as e:
+            for _ in range(3):
+                gh = e.graph(g)
+                st = e.run(gh)
+                res = (st,) + tuple(e.result(gh))
+                gh.destroy()
+                assert_same(res, ref, f"wavefront {geo}")
