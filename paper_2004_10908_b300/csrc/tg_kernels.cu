@@ -344,11 +344,10 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
     }
 }
 
-// kMod: the launch's graphs have module tasks (a separate variant, so that
-// launches without them carry none of that code).  At most 512 threads (16
-// worker warps): 128 registers per thread fill the SM.
+// The scheduler's body; kMod: the launch's graphs have module tasks (a
+// separate variant, so that launches without them carry none of that code).
 template <bool kServe, bool kMod>
-__global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
+__device__ __forceinline__ void sched_body(const KParams &p)
 {
     extern __shared__ u64 s_ring[];
     __shared__ u32 s_head, s_tail;
@@ -743,7 +742,7 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
         if (act) {
             u = (u32)e & kIdMask;
             strong = ((u32)e & kStrongBit) != 0u;
-            resumed = ((u32)e & kResumeBit) != 0u;
+            resumed = !kServe && ((u32)e & kResumeBit) != 0u;   // the server never chunks
             insum = (u32)(e >> 32);
         }
         uint4 imm = make_uint4(0, 0, 0, 0);
@@ -792,7 +791,7 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
         // payload chunking: a step runs at most p.chunk rounds of a task; a
         // task with more left re-queues itself with its partial state
         const u32 r_todo = resumed ? r_left : rounds;
-        const u32 r_now = (p.chunk != 0u && r_todo > p.chunk) ? p.chunk : r_todo;
+        const u32 r_now = (!kServe && p.chunk != 0u && r_todo > p.chunk) ? p.chunk : r_todo;   // (not in the server)
         const bool partial = act && !cont && c_status == 0 && r_now < r_todo;
         const u32 c = (act && !partial && (kind == TG_STATIC || cont)) ? succ_cnt : 0u;
         const u32 maxc = __reduce_max_sync(kFull, c);
@@ -1251,6 +1250,20 @@ __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
         p.stats[(size_t)blockIdx.x * ST_COUNT + threadIdx.x] = s_stats[threadIdx.x];
 }
 
+// One-shot launches (single graphs, batches): at most 512 threads (16 worker
+// warps), so that 128 registers per thread fill the SM.
+template <bool kMod>
+__global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
+{
+    sched_body<false, kMod>(p);
+}
+
+// The resident server (its blocks are at most half an SM).
+__global__ void serve_kernel(KParams p)
+{
+    sched_body<true, false>(p);
+}
+
 // ---------------------------------------------------------------------------
 // re-arm: state of every graph of the launch, queues, sources (Algorithm 8)
 // grid = (ceil(max_n / 1024), n_graphs)
@@ -1438,26 +1451,26 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dyn_smem > raised[dev]) {
-            e = cudaFuncSetAttribute(sched_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            e = cudaFuncSetAttribute(sched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
-            e = cudaFuncSetAttribute(sched_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            e = cudaFuncSetAttribute(sched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
-            e = cudaFuncSetAttribute(sched_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
             raised[dev] = dyn_smem;
         }
     }
     if (serve)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<true, false>, threads, dyn_smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, serve_kernel, threads, dyn_smem);
     // the variant with module tasks must fit the same block shape
     int with_mod = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&with_mod, sched_kernel<false, true>, threads, dyn_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&with_mod, sched_kernel<true>, threads, dyn_smem);
     if (e != cudaSuccess)
         return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false, false>, threads, dyn_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false>, threads, dyn_smem);
     if (e == cudaSuccess)
         *blocks_per_sm = std::min(*blocks_per_sm, with_mod);
     return e;
@@ -1483,12 +1496,12 @@ cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t
 {
     const size_t smem = sched_dyn_smem(p.smem_mask + 1u, (u32)threads / 32u);
     if (serve)
-        sched_kernel<true, false><<<blocks, threads, smem, st>>>(p);
+        serve_kernel<<<blocks, threads, smem, st>>>(p);
     else
         if (p.has_modules)
-            sched_kernel<false, true><<<blocks, threads, smem, st>>>(p);
+            sched_kernel<true><<<blocks, threads, smem, st>>>(p);
         else
-            sched_kernel<false, false><<<blocks, threads, smem, st>>>(p);
+            sched_kernel<false><<<blocks, threads, smem, st>>>(p);
     return cudaGetLastError();
 }
 
