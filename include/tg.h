@@ -123,11 +123,6 @@ typedef struct {
     uint64_t mem_budget_bytes; /* admission budget for graph memory [the node/edge pools] */
     uint64_t max_nodes;        /* node pool capacity [derived from the arena] */
     uint64_t max_edges;        /* edge pool capacity [derived from the arena] */
-    int32_t payload_chunk;     /* payload rounds a step runs per task before the task re-queues
-                                  itself with its partial state, so that lanes of one warp with
-                                  very different round counts do not wait on the longest; 0 = all
-                                  rounds in one step [0]; results are the same either way */
-    int32_t reserved;
 } tg_ctx_opts;
 
 /* Create a context on the current CUDA device.

@@ -103,12 +103,10 @@ enum StatIdx {
 constexpr u32 kEmpty32 = 0xFFFFFFFFu;
 constexpr u64 kEmpty = 0xFFFFFFFFFFFFFFFFull;
 constexpr u32 kStrongBit = 0x80000000u;   // in a ready entry's low word
-constexpr u32 kResumeBit = 0x40000000u;   // in a ready entry's low word: a chunked payload continues
-                                          // (the high word then carries its partial mixing state)
-constexpr u32 kIdMask = 0x3FFFFFFFu;      // the task part of a ready entry's low word
+constexpr u32 kIdMask = 0x7FFFFFFFu;      // the task part of a ready entry's low word
 constexpr u32 kInflight = 0x80000000u;    // in NodeSlot::cnt
 constexpr u32 kAwait = 0x40000000u;       // in NodeSlot::cnt: a module task waits for its composed graph
-constexpr u32 kMaxNodeIndex = 0x3FFFFFFEu;
+constexpr u32 kMaxNodeIndex = 0x7FFFFFFEu;
 constexpr u32 kSoleBit = 0x80000000u;     // in a static task's successor id: the target has
                                           // strong in-degree 1 (its join word is never used)
 constexpr u32 kChunkShift = 8;            // node ranges are allocated in 256-task chunks
@@ -145,7 +143,7 @@ struct KParams {
     u32 local_keep;        // shared-memory ring size above which new work goes public (0 = default)
     u32 thief_mode;        // 0 capped thief slots, 1 adaptive (parks and wake tickets)
     u32 has_modules;       // the launch's graphs compose other graphs (module tasks)
-    u32 chunk;             // payload rounds a step runs per task before it re-queues the rest (0 = all)
+    u32 pad5;
     u32 *thief_slots;      // max_thieves words, each on its own 128-byte line
     u64 time_limit_ns;
     u64 *trace;            // TG_OPT_TRACE: per task {start ns, publish ns} (may be null)

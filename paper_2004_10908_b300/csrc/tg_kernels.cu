@@ -47,24 +47,15 @@ __device__ __forceinline__ u32 mix32(u32 x)
 
 // Task payload: seed word from (id, iter, insum), then `rounds` x (add the
 // golden-ratio constant, mix).
-__device__ __forceinline__ u32 payload_seed(u32 id, u32 iter, u32 insum)
+__device__ __forceinline__ u32 task_payload(u32 id, u32 iter, u32 insum, u32 rounds)
 {
-    return (id * 0x9E3779B9U) ^ (iter * 0x85EBCA6BU) ^ (insum * 0xC2B2AE35U) ^ 0x27D4EB2FU;
-}
-
-__device__ __forceinline__ u32 payload_rounds(u32 x, u32 rounds)
-{
+    u32 x = (id * 0x9E3779B9U) ^ (iter * 0x85EBCA6BU) ^ (insum * 0xC2B2AE35U) ^ 0x27D4EB2FU;
 #pragma unroll 4
     for (u32 r = 0; r < rounds; ++r) {
         x += 0x9E3779B9U;
         x = mix32(x);
     }
     return x;
-}
-
-__device__ __forceinline__ u32 task_payload(u32 id, u32 iter, u32 insum, u32 rounds)
-{
-    return payload_rounds(payload_seed(id, iter, insum), rounds);
 }
 
 __device__ __forceinline__ u32 cond_hash(u32 seed, u32 id, u32 iter)
@@ -738,22 +729,18 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             act = false;
         }
         u32 u = 0, insum = 0;
-        bool strong = false, resumed = false;
+        bool strong = false;
         if (act) {
             u = (u32)e & kIdMask;
             strong = ((u32)e & kStrongBit) != 0u;
-            resumed = !kServe && ((u32)e & kResumeBit) != 0u;   // the server never chunks
             insum = (u32)(e >> 32);
         }
         uint4 imm = make_uint4(0, 0, 0, 0);
         uint2 stt = make_uint2(0, 0);
         u32 gid = 0;
-        u32 r_left = 0;   // a resumed payload: rounds still to run (kept in the output slot)
         if (act) {
             imm = ld_imm<kServe>(reinterpret_cast<const uint4 *>(&p.slots[u]));
             stt = __ldcg(reinterpret_cast<const uint2 *>(&p.slots[u].cnt));
-            if (resumed)
-                r_left = __ldcg(&p.outv[u]);
             gid = single ? p.single_gid : ld_imm<kServe>(&p.chunk_gid[u >> kChunkShift]);
         }
         if (act) {
@@ -788,12 +775,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         // kPerLaneMax successors each lane releases its own; otherwise the
         // edges are flattened over the warp (edge e belongs to the lane
         // whose exclusive prefix covers it) to spread a wide fan-out.
-        // payload chunking: a step runs at most p.chunk rounds of a task; a
-        // task with more left re-queues itself with its partial state
-        const u32 r_todo = resumed ? r_left : rounds;
-        const u32 r_now = (!kServe && p.chunk != 0u && r_todo > p.chunk) ? p.chunk : r_todo;   // (not in the server)
-        const bool partial = act && !cont && c_status == 0 && r_now < r_todo;
-        const u32 c = (act && !partial && (kind == TG_STATIC || cont)) ? succ_cnt : 0u;
+        const u32 c = (act && (kind == TG_STATIC || cont)) ? succ_cnt : 0u;
         const u32 maxc = __reduce_max_sync(kFull, c);
         const bool per_lane = maxc <= kPerLaneMax;
         if (traced) {
@@ -862,10 +844,10 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         // ---- payload
         const u32 x = cont ? __ldcg(&p.outv[u]) +
                                  (kind == TG_SUBFLOW ? vld32(&p.descs[ld_imm<kServe>(&p.edges[imm.x])].acc) : 0u)
-                           : (act ? payload_rounds(resumed ? insum : payload_seed(lid, iter, insum), r_now) : 0u);
+                           : (act ? task_payload(lid, iter, insum, rounds) : 0u);
         const u32 dg = cont ? stt.y : mix32(stt.y ^ x);
         // a static sink of a subflow copy adds its output to the copy's join value
-        const bool sink_acc = modules && act && !partial && c_status == 0 && kind == TG_STATIC && succ_cnt == 0u;
+        const bool sink_acc = modules && act && c_status == 0 && kind == TG_STATIC && succ_cnt == 0u;
         if (sink_acc)
             atomicAdd(&p.descs[gid].acc, x);
         if (traced) {
@@ -873,8 +855,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             mark(2);
         }
 
-        const bool run = act && c_status == 0 && !partial;
-        const u32 U = run ? ((kind == TG_STATIC || cont) ? succ_cnt : 1u) : (partial ? 1u : 0u);
+        const bool run = act && c_status == 0;
+        const u32 U = run ? ((kind == TG_STATIC || cont) ? succ_cnt : 1u) : 0u;
         // reserve the pending count of every activation this warp may push
         // before any of them becomes visible (a fence precedes publication)
         if (single) {
@@ -882,11 +864,11 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             if (lane == 0 && sumU)
                 atomicAdd(&p.descs[p.single_gid].pe, (u64)sumU);
         } else {
-            u32 rem = __ballot_sync(kFull, run || partial);
+            u32 rem = __ballot_sync(kFull, run);
             while (rem) {
                 int l = __ffs(rem) - 1;
                 u32 g = __shfl_sync(kFull, gid, l);
-                bool in = (run || partial) && gid == g;
+                bool in = run && gid == g;
                 u32 m = __ballot_sync(kFull, in);
                 u32 sumU = __reduce_add_sync(kFull, in ? U : 0u);
                 if (lane == l && sumU)
@@ -1042,11 +1024,6 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                     racy = pgo_[j];
         }
         stage(w, my_stage, ns, c_has, ((u64)x << 32) | (u64)c_t, lane, st_spill);
-        if (partial) {
-            __stcg(&p.outv[u], r_todo - r_now);   // read by the resumed step (after the fence or in hand)
-            mp++;
-        }
-        stage(w, my_stage, ns, partial, ((u64)x << 32) | kResumeBit | (u64)u, lane, st_spill);
         if (c_fl & kInflight)
             racy = gid;
         if (traced) {
@@ -1169,12 +1146,11 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             const u32 P = act ? mp : 0u;
             if (single) {
                 const u32 E = (u32)__popc(__ballot_sync(kFull, act));
-                const u32 Ex = (u32)__popc(__ballot_sync(kFull, act && !partial));   // executions done
                 const u32 sumP = __reduce_add_sync(kFull, P);
                 const u32 sumU = __reduce_add_sync(kFull, U);
                 if (lane == 0 && E) {
                     const long long d = (long long)sumP - (long long)sumU - (long long)E;
-                    pend_delta = ((u64)Ex << 32) + (u64)d;
+                    pend_delta = ((u64)E << 32) + (u64)d;   // (no continuations without modules)
                     pend_old = atomicAdd(&p.descs[p.single_gid].pe, pend_delta);
                     pend_g = p.single_gid;
                     pend_cap = single_cap;
@@ -1188,7 +1164,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                     bool in = act && gid == g;
                     u32 m = __ballot_sync(kFull, in);
                     // a continuation consumes its pending count but is no execution
-                    u32 mx = __ballot_sync(kFull, in && !cont && !partial);
+                    u32 mx = __ballot_sync(kFull, in && !cont);
                     u32 sumP = __reduce_add_sync(kFull, in ? P : 0u);
                     u32 sumU = __reduce_add_sync(kFull, in ? U : 0u);
                     if (lane == l) {

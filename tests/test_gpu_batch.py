@@ -170,26 +170,3 @@ def test_graph_autotune_keeps_results_and_caches(tmp_path):
         chosen2, ns2 = e.autotune(h, trials=1, cache_path=cache)
         assert chosen2 == chosen and ns2 == ns
         assert len(open(cache).read().splitlines()) == 1
-
-
-@pytest.mark.parametrize("chunk", [8, 64, 128])
-def test_payload_chunking_is_exact_in_batches(ex, chunk):
-    """Rounds U{8..512} per task, at most `chunk` rounds per step: every task
-    resumes from its partial state and ends with the oracle's results; the
-    execution counts are executions, not chunks."""
-    gs = w.config4(seed=16, n_graphs=48, n_lo=16, n_hi=3000)
-    hs = [ex.graph(g) for g in gs]
-    try:
-        ex.set_launch(payload_chunk=chunk)
-        assert ex.opts()["payload_chunk"] == chunk
-        b = ex.batch(hs)
-        b.launch()
-        st, sts = b.wait()
-        assert st == 0 and (sts == 0).all()
-        _check_against_oracle(ex, gs, hs)
-        assert ex.stats()["tasks"] == sum(int(oracle.run(g, exec_cap=200_000).execs) for g in gs)
-        b.destroy()
-    finally:
-        ex.set_launch()
-        for h in hs:
-            h.destroy()

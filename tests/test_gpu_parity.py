@@ -239,33 +239,6 @@ def test_adaptive_thieves_parity_and_fewer_wasted_steals():
     assert wasted[1] * 4 < wasted[0], wasted
 
 
-@pytest.mark.parametrize("chunk", [1, 5, 32])
-def test_payload_chunking_single_graphs(chunk):
-    """Chunked payloads on loops, branches, the paper's examples and racy
-    graphs: identical results, races still caught, the execution cap still
-    counts executions."""
-    from paper_2004_10908_b300 import Executor, STATUS_NAMES, binding as B
-    graphs = [w.config1(levels=5, width=30, trip=3, rounds=64), w.do_while(30, 40),
-              w.config3(seed=3, n_cond=40, body_levels=3, body_width=5, rounds=24, trip_max=5)] + \
-             [w.nested_loops(s, rounds=17) for s in range(5)]
-    with Executor(arena_bytes=1 << 29, payload_chunk=chunk) as e:
-        for g in graphs:
-            dev, ref = run_both(e, g)
-            assert_same(dev, ref, f"{g.name} chunk={chunk}")
-        racy = w.pitfall_race()
-        outs = pins.brute_force(racy, exec_cap=1 << 31, max_states=300000)
-        for _ in range(5):
-            gh = e.graph(racy)
-            st = e.run(gh)
-            out, cnt, dig, execs = e.result(gh)
-            gh.destroy()
-            mine = ("OK", tuple(int(x) for x in out), tuple(int(x) for x in cnt), tuple(int(x) for x in dig))
-            assert STATUS_NAMES[st] == "RACE" or mine in outs
-    with Executor(arena_bytes=1 << 28, payload_chunk=chunk, exec_cap=50) as e:
-        gh = e.graph(w.do_while(100, 64))
-        assert e.run(gh) == B.TG_ERR_EXEC_LIMIT
-        gh.destroy()
-
 
 def test_adaptive_thieves_finish_a_wide_wavefront():
     """Adaptive thieves with a short local backlog on a wide wavefront: busy
