@@ -259,7 +259,7 @@ __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u6
 // Examine the result of the previous iteration's pending-count update: a
 // graph whose pending count reached zero is complete; one whose execution
 // count passed its cap is poisoned with TG_ERR_EXEC_LIMIT.
-template <bool kServe, bool kMod>
+template <bool kServe, bool kExt>
 __device__ __forceinline__ u64 settle_finish(const KParams &p, bool &pend, u64 old, u64 delta, u32 g, u32 cap)
 {
     if (!pend)
@@ -269,7 +269,7 @@ __device__ __forceinline__ u64 settle_finish(const KParams &p, bool &pend, u64 o
     if ((u32)(nw >> 32) > cap)
         atomicCAS(&p.descs[g].status, 0, TG_ERR_EXEC_LIMIT);
     if ((u32)nw == 0u) {
-        const u32 ret = (!kServe && kMod) ? vld32(&p.descs[g].ret) : kEmpty32;
+        const u32 ret = (!kServe && kExt) ? vld32(&p.descs[g].ret) : kEmpty32;
         if (ret != kEmpty32) {
             // a composed graph is done: its module task resumes (a
             // continuation activation) and inherits its status
@@ -335,9 +335,11 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
     }
 }
 
-// The scheduler's body; kMod: the launch's graphs have module tasks (a
-// separate variant, so that launches without them carry none of that code).
-template <bool kServe, bool kMod>
+// The scheduler's body.  kExt: the launch uses an optional feature -- module
+// or subflow tasks, the adaptive thief mode or tracing -- which lives in a
+// separate variant, so that other launches carry none of that code (it costs
+// them 5-19 % per dependency hop, measured).
+template <bool kServe, bool kExt>
 __device__ __forceinline__ void sched_body(const KParams &p)
 {
     extern __shared__ u64 s_ring[];
@@ -370,8 +372,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     const bool race_check = (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
     const int bmax = (int)min(32u, max(1u, p.batch_max));
     // one graph: every activation has gid == single_gid (not when it composes others)
-    const bool single = !kServe && !kMod && p.lt == nullptr;
-    constexpr bool modules = !kServe && kMod;
+    const bool single = !kServe && !kExt && p.lt == nullptr;
+    constexpr bool modules = !kServe && kExt;
     const u32 single_cap = single ? ld_imm<kServe>(&p.descs[p.single_gid].exec_cap) : 0u;
     const u64 t0 = globaltimer();
     const u64 deadline = t0 + p.time_limit_ns;
@@ -408,7 +410,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         st_idle = 0, st_iters = 0, st_hand = 0, st_park = 0, st_fail = 0;
     // adaptive thieves (Alg. 3/6 invariant): a block is active while one of
     // its warps executes; blocks are the workers whose counts are kept
-    const bool adaptive = !kServe && p.thief_mode == 1u;
+    const bool adaptive = !kServe && kExt && p.thief_mode == 1u;
     bool busy_w = false;
     u32 rng = mix32(blockIdx.x * 0x9E3779B9U + (u32)warp * 0x85EBCA6BU + 1u);
     bool pend = false;      // a pending-count update whose result is not examined yet
@@ -428,7 +430,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
 
     // traced launches: cycles per phase of a step, marked by lane 0 (the
     // previous mark of each warp lives in shared memory)
-    const bool traced = p.trace != nullptr;
+    const bool traced = kExt && p.trace != nullptr;
     auto mark = [&](int phase) {
         if (traced && lane == 0) {
             const u64 t = clock64();
@@ -451,7 +453,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             if (k) {
                 st_local++;
             } else {
-                resume(settle_finish<kServe, kMod>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
+                resume(settle_finish<kServe, kExt>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
                 if (adaptive && busy_w) {
                     busy_w = false;
                     if (lane == 0 && atomicSub(&s_busy, 1u) == 1u)
@@ -832,14 +834,14 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         }
 
         // the previous iteration's pending-count update arrives meanwhile
-        resume(settle_finish<kServe, kMod>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
+        resume(settle_finish<kServe, kExt>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
 
         // a strong activation consumed its join word: re-arm it for the next
         // round (composes with releases of that round that arrive early)
         if (act && strong)
             atomicAdd(&p.slots[u].W, (u64)indeg - ((u64)insum << 32));
 
-        if (p.trace && act)
+        if (kExt && p.trace && act)
             p.trace[2ull * u] = globaltimer();
         // ---- payload
         const u32 x = cont ? __ldcg(&p.outv[u]) +
@@ -1124,7 +1126,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 }
             }
         }
-        if (p.trace && act)
+        if (kExt && p.trace && act)
             p.trace[2ull * u + 1ull] = globaltimer();
         // ---- a warp whose step produced at most kHandMax activations runs
         // them itself next (a chain never leaves the warp); wider output is
@@ -1202,7 +1204,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         }
     }
 
-    (void)settle_finish<kServe, kMod>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
+    (void)settle_finish<kServe, kExt>(p, pend, pend_old, pend_delta, pend_g, pend_cap);
     if (lane == 0) {
         atomicAdd(&s_stats[ST_POP_LOCAL], st_local);
         atomicAdd(&s_stats[ST_POP_OWN], st_own);
@@ -1228,10 +1230,10 @@ __device__ __forceinline__ void sched_body(const KParams &p)
 
 // One-shot launches (single graphs, batches): at most 512 threads (16 worker
 // warps), so that 128 registers per thread fill the SM.
-template <bool kMod>
+template <bool kExt>
 __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
 {
-    sched_body<false, kMod>(p);
+    sched_body<false, kExt>(p);
 }
 
 // The resident server (its blocks are at most half an SM).
@@ -1441,7 +1443,7 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
     }
     if (serve)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, serve_kernel, threads, dyn_smem);
-    // the variant with module tasks must fit the same block shape
+    // the extended variant must fit the same block shape
     int with_mod = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&with_mod, sched_kernel<true>, threads, dyn_smem);
     if (e != cudaSuccess)
@@ -1474,7 +1476,7 @@ cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t
     if (serve)
         serve_kernel<<<blocks, threads, smem, st>>>(p);
     else
-        if (p.has_modules)
+        if (p.has_modules || p.thief_mode == 1u || p.trace != nullptr)
             sched_kernel<true><<<blocks, threads, smem, st>>>(p);
         else
             sched_kernel<false><<<blocks, threads, smem, st>>>(p);

@@ -255,3 +255,22 @@ def test_adaptive_thieves_finish_a_wide_wavefront():
                 res = (st,) + tuple(e.result(gh))
                 gh.destroy()
                 assert_same(res, ref, f"wavefront {geo}")
+
+
+def test_tracing_keeps_results_and_records_times():
+    """TG_OPT_TRACE (the extended scheduler variant): same results; every
+    executed task has a start no later than its publish time, and the phase
+    cycle counters are filled."""
+    from paper_2004_10908_b300 import Executor, binding as B
+    g = w.config1(levels=4, width=50, trip=2, rounds=16)
+    ref = oracle.run(g)
+    with Executor(arena_bytes=1 << 28, flags=B.TG_OPT_TRACE) as e:
+        gh = e.graph(g)
+        st = e.run(gh)
+        assert_same((st,) + tuple(e.result(gh)), ref, "traced")
+        s = e.stats()
+        assert all(c > 0 for c in s["phase_cycles"])
+        t0, t1 = B.tg_trace_copy(e.ctx, gh.handle, g.n)
+        ran = ref.cnt > 0
+        assert (t0[ran] > 0).all() and (t1[ran] >= t0[ran]).all()
+        gh.destroy()
