@@ -339,7 +339,7 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
 // or subflow tasks, the adaptive thief mode or tracing -- which lives in a
 // separate variant, so that other launches carry none of that code (it costs
 // them 5-19 % per dependency hop, measured).
-template <bool kServe, bool kExt>
+template <bool kServe, bool kExt, bool kOne>
 __device__ __forceinline__ void sched_body(const KParams &p)
 {
     extern __shared__ u64 s_ring[];
@@ -372,7 +372,9 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     const bool race_check = (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
     const int bmax = (int)min(32u, max(1u, p.batch_max));
     // one graph: every activation has gid == single_gid (not when it composes others)
-    const bool single = !kServe && !kExt && p.lt == nullptr;
+    // kOne: a lean launch of one graph (no launch table); every activation
+    // then has gid == single_gid
+    constexpr bool single = !kServe && !kExt && kOne;
     constexpr bool modules = !kServe && kExt;
     const u32 single_cap = single ? ld_imm<kServe>(&p.descs[p.single_gid].exec_cap) : 0u;
     const u64 t0 = globaltimer();
@@ -1229,17 +1231,17 @@ __device__ __forceinline__ void sched_body(const KParams &p)
 }
 
 // One-shot launches (single graphs, batches): at most 512 threads (16 worker
-// warps), so that 128 registers per thread fill the SM.
-template <bool kExt>
+// warps), so that 128 registers per thread fill the SM.  kOne: one graph.
+template <bool kExt, bool kOne>
 __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
 {
-    sched_body<false, kExt>(p);
+    sched_body<false, kExt, kOne>(p);
 }
 
 // The resident server (its blocks are at most half an SM).
 __global__ void serve_kernel(KParams p)
 {
-    sched_body<true, false>(p);
+    sched_body<true, false, false>(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -1429,10 +1431,13 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dyn_smem > raised[dev]) {
-            e = cudaFuncSetAttribute(sched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            e = cudaFuncSetAttribute(sched_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
-            e = cudaFuncSetAttribute(sched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            e = cudaFuncSetAttribute(sched_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            if (e != cudaSuccess)
+                return e;
+            e = cudaFuncSetAttribute(sched_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
             e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
@@ -1444,13 +1449,16 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
     if (serve)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, serve_kernel, threads, dyn_smem);
     // the extended variant must fit the same block shape
-    int with_mod = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&with_mod, sched_kernel<true>, threads, dyn_smem);
+    int ext = 0, one = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ext, sched_kernel<true, false>, threads, dyn_smem);
     if (e != cudaSuccess)
         return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false>, threads, dyn_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&one, sched_kernel<false, true>, threads, dyn_smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false, false>, threads, dyn_smem);
     if (e == cudaSuccess)
-        *blocks_per_sm = std::min(*blocks_per_sm, with_mod);
+        *blocks_per_sm = std::min(*blocks_per_sm, std::min(ext, one));
     return e;
 }
 
@@ -1477,9 +1485,11 @@ cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t
         serve_kernel<<<blocks, threads, smem, st>>>(p);
     else
         if (p.has_modules || p.thief_mode == 1u || p.trace != nullptr)
-            sched_kernel<true><<<blocks, threads, smem, st>>>(p);
+            sched_kernel<true, false><<<blocks, threads, smem, st>>>(p);
+        else if (p.lt == nullptr)
+            sched_kernel<false, true><<<blocks, threads, smem, st>>>(p);
         else
-            sched_kernel<false><<<blocks, threads, smem, st>>>(p);
+            sched_kernel<false, false><<<blocks, threads, smem, st>>>(p);
     return cudaGetLastError();
 }
 
