@@ -385,6 +385,15 @@ int tg_run_noalloc(uint32_t n_nodes, const uint8_t *kinds, const uint32_t *param
  * option. */
 int tg_trace_copy(tg_ctx *ctx, const tg_graph *g, uint64_t *start_ns, uint64_t *end_ns);
 
+/* The packed form of g as Graphviz DOT text: one node per task ("<id> <kind>
+ * R=<rounds>", with the trip or constant of a condition and the composed
+ * graph of a module or subflow task) and its edges in insertion order --
+ * strong edges solid, weak edges dashed and labelled with their successor
+ * index.  Read back from the device, so it shows what the scheduler runs.
+ * *len receives the text's length (without the terminating NUL); the text is
+ * written only if buf holds len + 1 bytes, else TG_ERR_BUDGET. */
+int tg_graph_dot(tg_ctx *ctx, const tg_graph *g, char *buf, size_t cap, size_t *len);
+
 const char *tg_strerror(int status);
 
 #ifdef __cplusplus

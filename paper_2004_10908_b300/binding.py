@@ -108,6 +108,7 @@ SIGNATURES = {
     "tg_levelize": (ctypes.c_int, [_u32, _u32, _vp, _vp, _vp, _vp, ctypes.POINTER(_u32)]),
     "tg_stream_plan": (ctypes.c_int, [_u32, _u32, _vp, _vp, _u32, _vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     "tg_capture_run": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_u64)]),
+    "tg_graph_dot": (ctypes.c_int, [_vp, _vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "tg_run_noalloc": (ctypes.c_int, [_u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]),
     "tg_trace_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "tg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -357,6 +358,17 @@ def tg_stream_plan(n, src, dst, max_streams):
     st = load().tg_stream_plan(n, len(s), sp, dp, max_streams, stream.ctypes.data_as(_vp), ctypes.byref(ne),
                                ctypes.byref(nw))
     return st, stream, ne.value, nw.value
+
+
+def tg_graph_dot(ctx, g) -> str:
+    """The packed graph as Graphviz DOT text."""
+    n = ctypes.c_size_t(0)
+    st = load().tg_graph_dot(_vp(ctx), _vp(g), None, 0, ctypes.byref(n))
+    if st not in (TG_OK, TG_ERR_BUDGET):
+        raise TgError(st, "tg_graph_dot")
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(load().tg_graph_dot(_vp(ctx), _vp(g), buf, n.value + 1, ctypes.byref(n)), "tg_graph_dot")
+    return buf.value.decode()
 
 
 def tg_capture_run(ctx, g, max_streams):

@@ -1191,6 +1191,60 @@ int tg_stream_plan(uint32_t n, uint32_t m, const uint32_t *src, const uint32_t *
     return TG_OK;
 }
 
+int tg_graph_dot(tg_ctx *c, const tg_graph *g, char *buf, size_t cap, size_t *len)
+{
+    if (!c || !g || g->ctx != c || !len)
+        return TG_ERR_INVALID;
+    const tg_graph *t = g->tmpl ? g->tmpl : g;
+    std::vector<NodeSlot> rec(g->n);
+    std::vector<u32> ed(t->pristine_off - t->edge_off);
+    if (!c->serving)
+        TG_CUDA(cudaStreamSynchronize(c->stream));
+    TG_CUDA(cudaMemcpy(rec.data(), c->edges + t->pristine_off, (size_t)g->n * sizeof(NodeSlot),
+                       cudaMemcpyDeviceToHost));
+    if (!ed.empty())
+        TG_CUDA(cudaMemcpy(ed.data(), c->edges + t->edge_off, ed.size() * 4, cudaMemcpyDeviceToHost));
+    static const char *kind_name[] = {"static", "branch", "loop", "const", "module", "subflow"};
+    std::string s = "digraph tg {\n  node [shape=box];\n";
+    char line[160];
+    for (u32 v = 0; v < g->n; ++v) {
+        const u32 kind = (rec[v].prm >> 16) & 0xFFu;
+        const u32 arg = rec[v].prm >> 24;
+        const u32 rounds = rec[v].prm & 0xFFFFu;
+        const u64 first = rec[v].succ_off - t->edge_off;
+        int k = std::snprintf(line, sizeof(line), "  n%u [label=\"%u %s R=%u", v, v, kind <= TG_SUBFLOW ? kind_name[kind] : "?",
+                              rounds);
+        if (kind == TG_COND_LOOP)
+            k += std::snprintf(line + k, sizeof(line) - k, " T=%u", arg);
+        else if (kind == TG_COND_CONST)
+            k += std::snprintf(line + k, sizeof(line) - k, " r=%d", (int)(signed char)(unsigned char)arg);
+        else if (kind >= TG_MODULE && first < ed.size())
+            k += std::snprintf(line + k, sizeof(line) - k, " graph=%u", ed[first]);
+        std::snprintf(line + k, sizeof(line) - k, "\"%s];\n", kind >= TG_COND_BRANCH && kind <= TG_COND_CONST ? ", shape=diamond" : "");
+        s += line;
+    }
+    for (u32 v = 0; v < g->n; ++v) {
+        const u32 kind = (rec[v].prm >> 16) & 0xFFu;
+        const u32 cnt = rec[v].deg & 0xFFFFu;
+        const u64 first = rec[v].succ_off - t->edge_off + (kind >= TG_MODULE ? 1u : 0u);
+        const bool weak = kind >= TG_COND_BRANCH && kind <= TG_COND_CONST;
+        for (u32 j = 0; j < cnt && first + j < ed.size(); ++j) {
+            const u32 d = ed[first + j] & ~kSoleBit;
+            if (weak)
+                std::snprintf(line, sizeof(line), "  n%u -> n%u [style=dashed, label=\"%u\"];\n", v, d, j);
+            else
+                std::snprintf(line, sizeof(line), "  n%u -> n%u;\n", v, d);
+            s += line;
+        }
+    }
+    s += "}\n";
+    *len = s.size();
+    if (!buf || cap < s.size() + 1)
+        return TG_ERR_BUDGET;
+    std::memcpy(buf, s.c_str(), s.size() + 1);
+    return TG_OK;
+}
+
 int tg_capture_run(tg_ctx *c, tg_graph *g, uint32_t max_streams, uint64_t *ns)
 {
     if (!c || !g || g->ctx != c || max_streams == 0 || max_streams > 32 || g->n > 65536u || g->n_cond != 0 ||

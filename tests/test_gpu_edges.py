@@ -80,3 +80,46 @@ def test_exec_cap_of_one():
         assert e.run(two) == B.TG_ERR_EXEC_LIMIT
         assert oracle.run(from_lists("two", [STATIC, STATIC], pack_param([1, 1]), [(0, 1)]),
                           exec_cap=1).status == oracle.EXEC_LIMIT
+
+
+def test_dot_dump_shows_the_packed_graph(ex):
+    """The DOT text read back from the device lists every task with its kind
+    and rounds, and every edge in insertion order: strong solid, weak dashed
+    with its successor index."""
+    import re
+    from paper_2004_10908_b300 import binding as B
+    from workloads.graphs import COND_BRANCH, COND_LOOP, MODULE, SUBFLOW
+    inner = ex.graph(w.diamond())
+    kinds = [STATIC, COND_BRANCH, STATIC, STATIC, COND_LOOP, MODULE, SUBFLOW, COND_CONST, STATIC]
+    params = [pack_param(5), pack_param(6), pack_param(7), pack_param(8), pack_param(9, 3), pack_param(10),
+              pack_param(11), pack_param(12, 0, -1 & 0xFF), pack_param(13)]
+    edges = [(0, 1), (1, 2), (1, 3), (2, 4), (3, 4), (4, 2), (4, 5), (5, 6), (6, 7), (7, 8), (0, 8)]
+    g = from_lists("all_kinds", kinds, params, edges)
+    h = ex.graph(g, modules={5: inner, 6: inner})
+    text = B.tg_graph_dot(ex.ctx, h.handle)
+    nodes = dict(re.findall(r'n(\d+) \[label="\d+ (\w+) R=', text))
+    names = {STATIC: "static", COND_BRANCH: "branch", COND_LOOP: "loop", COND_CONST: "const",
+             MODULE: "module", SUBFLOW: "subflow"}
+    assert {int(k): v for k, v in nodes.items()} == {v: names[k] for v, k in enumerate(kinds)}
+    assert "T=3" in text and "r=-1" in text and "graph=" in text
+    got = [(int(a), int(b), lab) for a, b, _, lab in re.findall(r'n(\d+) -> n(\d+)( \[style=dashed, label="(\d+)"\])?;', text)]
+    want = []
+    for s in range(len(kinds)):
+        succ = [d for a, d in edges if a == s]
+        cond = kinds[s] in (COND_BRANCH, COND_LOOP, COND_CONST)
+        want += [(s, d, str(j) if cond else "") for j, d in enumerate(succ)]
+    assert got == want
+    h.destroy()
+    inner.destroy()
+
+
+def test_deadlocked_join_ends_without_running_it(ex):
+    """A strong merge after a branch: only one arm runs, so the join's count
+    never reaches zero; the run still ends (nothing queued or running) and
+    the join has run zero times."""
+    from workloads.graphs import COND_BRANCH
+    g = from_lists("dead_join", [STATIC, COND_BRANCH, STATIC, STATIC, STATIC],
+                   pack_param([3] * 5), [(0, 1), (1, 2), (1, 3), (2, 4), (3, 4)])
+    dev, ref = run_both(ex, g)
+    assert_same(dev, ref, g.name)
+    assert ref.status == oracle.OK and ref.cnt[4] == 0 and ref.cnt[2] + ref.cnt[3] == 1
