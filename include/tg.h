@@ -166,9 +166,11 @@ int tg_graph_create(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const u
  * exists (TG_ERR_BUSY).  A graph with
  * module tasks runs with tg_run / tg_submit: each launch starts every graph
  * it composes (transitively) from its initial state, and afterwards
- * tg_result_copy on a composed graph reads its tasks' results.  Batches,
- * instances, the resident server and tg_capture_run refuse graphs with
- * module tasks (TG_ERR_INVALID).  TG_ERR_INVALID also for a module task
+ * tg_result_copy on a composed graph reads its tasks' results.  Batches may
+ * hold such graphs (each launch re-arms every graph their compositions
+ * reach; two members composing one graph run into each other: a race);
+ * instances, the resident server and tg_capture_run refuse them
+ * (TG_ERR_INVALID).  TG_ERR_INVALID also for a module task
  * without a graph, a graph given for another kind, or a foreign graph. */
 int tg_graph_create_composed(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
                              uint32_t n_edges, const uint32_t *src, const uint32_t *dst,

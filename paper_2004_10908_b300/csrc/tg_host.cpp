@@ -132,6 +132,8 @@ struct tg_graph {
 struct tg_batch {
     tg_ctx *ctx = nullptr;
     std::vector<tg_graph *> gs;
+    std::vector<tg_graph *> comp;   // graphs its members' module and subflow tasks reach
+    bool has_mod = false;
     u64 lt_off = 0, lt_len = 0;
     u32 max_n = 0, total_src = 0;
     Geometry geo;
@@ -904,6 +906,28 @@ int tg_graph_get_info(const tg_graph *g, tg_graph_info *info)
 
 static int serve_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket);
 
+// Every graph that the module and subflow tasks of `roots` reach
+// (transitively), the roots themselves excluded.
+static std::vector<tg_graph *> composition_closure(const std::vector<tg_graph *> &roots)
+{
+    std::vector<tg_graph *> todo, seen;
+    for (tg_graph *r : roots) {
+        todo.insert(todo.end(), r->mods.begin(), r->mods.end());
+        todo.insert(todo.end(), r->sub_insts.begin(), r->sub_insts.end());
+    }
+    while (!todo.empty()) {
+        tg_graph *mg = todo.back();
+        todo.pop_back();
+        if (std::find(roots.begin(), roots.end(), mg) != roots.end() ||
+            std::find(seen.begin(), seen.end(), mg) != seen.end())
+            continue;
+        seen.push_back(mg);
+        todo.insert(todo.end(), mg->mods.begin(), mg->mods.end());
+        todo.insert(todo.end(), mg->sub_insts.begin(), mg->sub_insts.end());
+    }
+    return seen;
+}
+
 int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
 {
     if (!c || !g || g->ctx != c || !ticket)
@@ -932,19 +956,8 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     p.total_sources = g->n_src;
     if (g->n_mod) {
         // every graph the composition reaches starts idle from its initial state
-        std::vector<tg_graph *> todo(g->mods.begin(), g->mods.end()), seen;
-        todo.insert(todo.end(), g->sub_insts.begin(), g->sub_insts.end());
-        while (!todo.empty()) {
-            tg_graph *mg = todo.back();
-            todo.pop_back();
-            if (mg == g || std::find(seen.begin(), seen.end(), mg) != seen.end())
-                continue;
-            seen.push_back(mg);
-            todo.insert(todo.end(), mg->mods.begin(), mg->mods.end());
-            todo.insert(todo.end(), mg->sub_insts.begin(), mg->sub_insts.end());
-        }
         p.has_modules = 1u;
-        for (tg_graph *mg : seen) {
+        for (tg_graph *mg : composition_closure({g})) {
             if (mg->ready)
                 TG_CUDA(cudaStreamWaitEvent(c->stream, mg->ready, 0));
             TG_CUDA(launch_module_rearm(p, mg->gid, mg->n, c->stream));
@@ -1391,6 +1404,7 @@ static int batch_capture(tg_ctx *c, tg_batch *b)
     p.single_gid = 0;
     p.max_n = b->max_n;
     p.total_sources = b->total_src;
+    p.has_modules = b->has_mod ? 1u : 0u;
     b->kp = p;
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
@@ -1400,7 +1414,11 @@ static int batch_capture(tg_ctx *c, tg_batch *b)
     cudaStream_t cs = c->capture_stream;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return TG_ERR_CUDA;
-    cudaError_t e1 = launch_rearm(p, cs);
+    cudaError_t e0 = cudaSuccess;
+    for (tg_graph *mg : b->comp)   // composed graphs and subflow copies start idle
+        if (e0 == cudaSuccess)
+            e0 = launch_module_rearm(p, mg->gid, mg->n, cs);
+    cudaError_t e1 = e0 != cudaSuccess ? e0 : launch_rearm(p, cs);
     cudaError_t e2 = launch_sched(p, b->geo.blocks, b->geo.threads, cs);
     cudaError_t e3 = launch_finalize(p, cs);
     cudaError_t e4 = cudaStreamEndCapture(cs, &graph);
@@ -1425,7 +1443,7 @@ int tg_batch_create(tg_ctx *c, tg_graph *const *gs, uint32_t n, tg_batch **out)
     u64 inj = 0;
     u32 max_n = 0;
     for (u32 i = 0; i < n; ++i) {
-        if (!gs[i] || gs[i]->ctx != c || gs[i]->n_mod)
+        if (!gs[i] || gs[i]->ctx != c)
             return TG_ERR_INVALID;
         for (u32 j = 0; j < i; ++j)
             if (gs[j] == gs[i])
@@ -1455,6 +1473,10 @@ int tg_batch_create(tg_ctx *c, tg_graph *const *gs, uint32_t n, tg_batch **out)
     b->max_n = max_n;
     b->total_src = (u32)inj;
     b->geo = c->geo;
+    for (tg_graph *g : b->gs)
+        b->has_mod = b->has_mod || g->n_mod != 0;
+    if (b->has_mod)
+        b->comp = composition_closure(b->gs);
     int rc = batch_capture(c, b);
     if (rc != TG_OK) {
         tg_batch_destroy(c, b);
@@ -1489,6 +1511,9 @@ int tg_batch_launch(tg_ctx *c, tg_batch *b)
         if (g->ready)
             TG_CUDA(cudaStreamWaitEvent(c->stream, g->ready, 0));
     }
+    for (tg_graph *g : b->comp)
+        if (g->ready)
+            TG_CUDA(cudaStreamWaitEvent(c->stream, g->ready, 0));
     TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
     TG_CUDA(cudaGraphLaunch(b->exec, c->stream));
     TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));

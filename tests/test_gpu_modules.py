@@ -126,8 +126,6 @@ def test_refusals_and_standalone_use(ex):
     h1 = ex.graph(g1)
     ht = ex.graph(top, modules={1: h1})
     assert B.tg_instance_create(ex.ctx, ht.handle)[0] == B.TG_ERR_INVALID
-    st, _ = B.tg_batch_create(ex.ctx, [ht.handle])
-    assert st == B.TG_ERR_INVALID
     assert ex.capture_run(ht, 2)[0] == B.TG_ERR_INVALID
     assert B.tg_graph_destroy(ex.ctx, h1.handle) == B.TG_ERR_BUSY        # still composed
     # module task without a graph, a graph for a static task
@@ -198,3 +196,54 @@ def test_subflow_refusals(ex):
     comp.destroy()
     assert B.tg_graph_destroy(ex.ctx, hi.handle) == 0
     hi.handle = None
+
+
+def test_composed_graphs_in_a_batch(ex):
+    """A batch of composed graphs -- module loops, parallel subflows, plain
+    members -- in one captured launch, replayed: every member and every
+    composed graph ends with the composed oracle's results."""
+    mods = [w.diamond(R), w.nested_loops(5)]
+    tmpl = w.config2a(seed=13, levels=3, width=20, rounds=4)
+    hm = [ex.graph(g) for g in mods]
+    ht = ex.graph(tmpl)
+    members, refs = [], []
+    for i in range(6):
+        T = 2 + i
+        loop = from_lists(f"loop{i}", [STATIC, MODULE, COND_LOOP, STATIC],
+                          [pack_param(R), pack_param(R), pack_param(R, T), pack_param(R)],
+                          [(0, 1), (1, 2), (2, 1), (2, 3)])
+        fan = from_lists(f"fan{i}", [STATIC, SUBFLOW, SUBFLOW, STATIC], pack_param([R] * 4),
+                         [(0, 1), (0, 2), (1, 3), (2, 3)])
+        # each loop member composes its own graph (no two members share one)
+        mg = ex.graph(mods[i % 2]) if i >= 2 else hm[i]
+        members.append((ex.graph(loop, modules={1: mg}), loop, {"m": mods[i % 2], "t": loop}, {"t": {1: "m"}}, mg))
+        members.append((ex.graph(fan, modules={1: ht, 2: ht}), fan, {"s": tmpl, "t": fan}, {"t": {1: "s", 2: "s"}}, None))
+    plain = w.config1(levels=3, width=20, trip=2, rounds=8)
+    hp = ex.graph(plain)
+    b = ex.batch([m[0] for m in members] + [hp])
+    for _ in range(2):
+        b.launch()
+        st, sts = b.wait()
+        assert st == 0 and (sts == 0).all()
+        for h, top, graphs, mmap, mg in members:
+            ref = oc.run(graphs, mmap, "t")
+            out, cnt, dig, execs = ex.result(h)
+            np.testing.assert_array_equal(cnt, ref["t"][2], err_msg=top.name)
+            np.testing.assert_array_equal(out, ref["t"][1], err_msg=top.name)
+            np.testing.assert_array_equal(dig, ref["t"][3], err_msg=top.name)
+            if mg is not None:
+                mout, mcnt, mdig, _ = ex.result(mg)
+                np.testing.assert_array_equal(mcnt, ref["m"][2], err_msg=top.name + " module")
+                np.testing.assert_array_equal(mout, ref["m"][1], err_msg=top.name + " module")
+        pref = oracle.run(plain)
+        np.testing.assert_array_equal(ex.result(hp)[1], pref.cnt)
+    b.destroy()
+    for h, _, _, _, mg in members:
+        h.destroy()
+    for h, _, _, _, mg in members:
+        if mg is not None and mg not in hm:
+            mg.destroy()
+    hp.destroy()
+    ht.destroy()
+    for h in hm:
+        h.destroy()
