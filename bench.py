@@ -5,12 +5,24 @@ layered random DAG (in-degree U{1..8}, 16 rounds) and the 1024 x 1024
 wavefront (256 rounds), 2,048,576 task executions per step.  One step = for
 each graph: re-arm its state (join words, counts, digests, queues, sources),
 run the persistent scheduler until every task ran, finalise the status.
-Graph inputs are resident in HBM when the timed region starts; L2 (126 MB)
-is flushed between timed steps by writing a 512 MB buffer.
+Each graph runs at the launch geometry its own autotuning picked (before
+timing).  Graph inputs are resident in HBM when the timed region starts; L2
+(126 MB) is flushed between timed steps by writing a 512 MB buffer.
 
 Measured in the same run and reported beside it:
+  roofline / alu / atomics   the scheduler kernel against the measured HBM
+            copy bandwidth (with DRAM traffic from an ncu capture), the
+            integer-ALU ceiling and the atomic ceiling
+  critical_path   each graph's dependency floor (its longest path's payloads
+            run back to back by one thread) against its scheduler time
+  thief_policies  capped vs adaptive thieves (Alg. 3/6): time, failed rounds
+  capturer_baseline  Algorithm 1's CUDA graph of per-task kernels vs the
+            persistent scheduler on static DAGs
+  composition   module tasks in a loop and parallel joined subflows in one
+            launch vs the host re-running the composed graph
   batched   4,096 motif graphs (33M tasks) in one CUDA-graph-captured
             persistent launch, autotuned, versus one launch + sync per graph
+            and the oracle on every host core
   serving   Poisson request streams at 1k / 10k / 50k requests/s through the
             resident scheduler (p50 / p99 latency, tasks/s) versus serving the
             same stream one launch per request

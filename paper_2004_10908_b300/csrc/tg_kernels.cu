@@ -15,6 +15,12 @@
 //     overflow.
 // All rings are multi-producer multi-consumer with monotonically increasing
 // 32-bit tickets and an EMPTY marker per slot; every wait is bounded.
+// Module tasks run another graph to completion and resume as a continuation
+// (Composable Tasking); subflow tasks do the same on a fresh copy of a
+// template (Dynamic Tasking).  The scheduler comes in four compiled
+// variants: lean one-shot kernels for one graph and for batches, an
+// extended one-shot kernel with the optional features (module and subflow
+// tasks, adaptive thieves, tracing), and the resident server.
 #include <mutex>
 
 #include "tg_internal.h"
