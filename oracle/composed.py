@@ -25,7 +25,15 @@ after the module rules:
     task's output as their input sum, runs it to completion, and releases its
     own successors with its output plus the sum of the outputs of every
     execution of a static task without successors in that copy (the join
-    value, mod 2^32); copies spawned by different tasks are independent.
+    value, mod 2^32); copies spawned by different tasks are independent;
+  - a detached subflow task (bit 0 of its parameter word's top byte set)
+    releases its successors at once with its own output; its copy runs on
+    its own and the run ends only when the copy has ended too.  Nothing of
+    the copy flows back, so running it to completion at the spawn gives the
+    same results as any interleaving.
+
+run() also reports, under the key "*", the executions of every graph of the
+run, spawned copies included.
 
 graphs: dict key -> workloads.Graph; modules: dict key -> {task: key of the
 graph it composes, or of the template it spawns}; kinds use 4 for a module
@@ -76,6 +84,7 @@ def run(graphs, modules, root, exec_cap=DEFAULT_EXEC_CAP):
     """Returns {key: (status, out, cnt, dig, execs)} for every graph of the
     composition reachable from `root` (status is the run's status)."""
     states = {}
+    copies = []
 
     def state(key):
         if key not in states:
@@ -118,8 +127,12 @@ def run(graphs, modules, root, exec_cap=DEFAULT_EXEC_CAP):
             if kind == MODULE:
                 run_graph(modules[key][v], x)   # the composed graph runs to completion first
             elif kind == SUBFLOW:
-                tmpl = modules[key][v]         # a fresh copy of the template, joined
-                x = (x + run_graph(tmpl, x, _State(graphs[tmpl]))) & 0xFFFFFFFF
+                tmpl = modules[key][v]         # a fresh copy of the template
+                copy = _State(graphs[tmpl])
+                copies.append(copy)
+                copy_sum = run_graph(tmpl, x, copy)
+                if not (st.params[v] >> 24) & 1:   # joined: the join value flows on
+                    x = (x + copy_sum) & 0xFFFFFFFF
             for u in st.succ[v]:
                 st.w_sum[u] = (st.w_sum[u] + x) & 0xFFFFFFFF
                 st.w_cnt[u] -= 1
@@ -139,4 +152,5 @@ def run(graphs, modules, root, exec_cap=DEFAULT_EXEC_CAP):
     for key, st in states.items():
         res[key] = (status, np.array(st.out, np.uint32), np.array(st.cnt, np.uint32),
                     np.array(st.dig, np.uint32), st.execs)
+    res["*"] = sum(st.execs for st in states.values()) + sum(c.execs for c in copies)
     return res

@@ -161,3 +161,26 @@ def test_parallel_subflows_of_one_template_are_independent():
     as_mod = oc.run({"n": tmpl, "t": seq_mod}, {"t": {1: "n", 2: "n"}}, "t")["t"]
     assert as_sub[0] == as_mod[0] == oracle.OK
     assert as_sub[1][3] != as_mod[1][3]    # join values differ from the module's plain output
+
+
+def test_detached_subflow_releases_at_once_and_still_runs():
+    """A detached subflow (Dynamic Tasking's detach): B's successors get B's
+    own output, and the copy's executions still count in the run."""
+    from workloads.graphs import SUBFLOW
+    sub = from_lists("B_subflow", [STATIC] * 3, pack_param([R] * 3), [(0, 2), (1, 2)])
+    det = from_lists("fig_det", [STATIC, SUBFLOW, STATIC, STATIC],
+                     [pack_param(R), pack_param(R, 0, 1), pack_param(R), pack_param(R)],
+                     [(0, 1), (0, 2), (1, 3), (2, 3)])
+    res = oc.run({"s": sub, "t": det}, {"t": {1: "s"}}, "t")
+    st, out, cnt, dig, execs = res["t"]
+    assert st == oracle.OK and list(cnt) == [1, 1, 1, 1]
+    a = oracle.payload(0, 0, 0, R)
+    b = oracle.payload(1, 0, a, R)
+    c = oracle.payload(2, 0, a, R)
+    d = oracle.payload(3, 0, (b + c) & 0xFFFFFFFF, R)    # no join value
+    assert list(out) == [a, b, c, d]
+    assert res["*"] == 4 + 3
+    joined = from_lists("fig", [STATIC, SUBFLOW, STATIC, STATIC], pack_param([R] * 4),
+                        [(0, 1), (0, 2), (1, 3), (2, 3)])
+    rj = oc.run({"s": sub, "t": joined}, {"t": {1: "s"}}, "t")
+    assert rj["t"][1][3] != d and rj["*"] == 7
