@@ -75,7 +75,11 @@ typedef struct tg_batch tg_batch;
  * copy completes, the task's successors are released with its output plus
  * the sum (mod 2^32) of the outputs of every execution of a static task
  * without successors in the copy.  Each subflow task owns one copy, so
- * subflows of different tasks run concurrently. */
+ * subflows of different tasks run concurrently.  With bit 24 of its
+ * parameter word set the subflow is detached: the task's successors are
+ * released at once with its output, the copy runs on its own, and the run
+ * (or the composed graph holding the task) ends only when the copy has
+ * ended too; running the task again while its copy still runs is a race. */
 enum { TG_STATIC = 0, TG_COND_BRANCH = 1, TG_COND_LOOP = 2, TG_COND_CONST = 3, TG_MODULE = 4,
        TG_SUBFLOW = 5 };
 

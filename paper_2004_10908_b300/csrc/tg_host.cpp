@@ -689,8 +689,8 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
         u32 arg = 0;
         if (kind == TG_COND_LOOP)
             arg = (params[v] >> 16) & 0xFFu;
-        else if (kind == TG_COND_CONST)
-            arg = params[v] >> 24;
+        else if (kind == TG_COND_CONST || kind == TG_SUBFLOW)
+            arg = params[v] >> 24;   // the constant; a subflow's detach bit
         s.succ_off = edge_base + acc;
         s.deg = outdeg[v] | (sin[v] << 16);
         s.prm = (params[v] & 0xFFFFu) | (kind << 16) | (arg << 24);
@@ -1232,7 +1232,8 @@ int tg_graph_dot(tg_ctx *c, const tg_graph *g, char *buf, size_t cap, size_t *le
         else if (kind == TG_COND_CONST)
             k += std::snprintf(line + k, sizeof(line) - k, " r=%d", (int)(signed char)(unsigned char)arg);
         else if (kind >= TG_MODULE && first < ed.size())
-            k += std::snprintf(line + k, sizeof(line) - k, " graph=%u", ed[first]);
+            k += std::snprintf(line + k, sizeof(line) - k, " graph=%u%s", ed[first],
+                               (kind == TG_SUBFLOW && (arg & 1u)) ? " detached" : "");
         std::snprintf(line + k, sizeof(line) - k, "\"%s];\n", kind >= TG_COND_BRANCH && kind <= TG_COND_CONST ? ", shape=diamond" : "");
         s += line;
     }

@@ -106,6 +106,8 @@ constexpr u32 kStrongBit = 0x80000000u;   // in a ready entry's low word
 constexpr u32 kIdMask = 0x7FFFFFFFu;      // the task part of a ready entry's low word
 constexpr u32 kInflight = 0x80000000u;    // in NodeSlot::cnt
 constexpr u32 kAwait = 0x40000000u;       // in NodeSlot::cnt: a module task waits for its composed graph
+constexpr u32 kDetachBit = 0x80000000u;   // in GDesc::ret: the copy of a detached subflow (holds a
+                                          // token of its parent graph's pending count)
 constexpr u32 kMaxNodeIndex = 0x7FFFFFFEu;
 constexpr u32 kSoleBit = 0x80000000u;     // in a static task's successor id: the target has
                                           // strong in-degree 1 (its join word is never used)

@@ -275,8 +275,29 @@ __device__ __forceinline__ u64 settle_finish(const KParams &p, bool &pend, u64 o
     if ((u32)(nw >> 32) > cap)
         atomicCAS(&p.descs[g].status, 0, TG_ERR_EXEC_LIMIT);
     if ((u32)nw == 0u) {
-        const u32 ret = (!kServe && kExt) ? vld32(&p.descs[g].ret) : kEmpty32;
-        if (ret != kEmpty32) {
+        u32 ret = (!kServe && kExt) ? vld32(&p.descs[g].ret) : kEmpty32;
+        // a detached subflow's copy is done: it gives back its token of the
+        // parent graph's pending count, which may complete the parent in turn
+        // (bounded: a template holds no subflow tasks, so one level at most)
+        for (int hop = 0; !kServe && kExt && ret != kEmpty32 && (ret & kDetachBit) != 0u && hop < 2; ++hop) {
+            const u32 parent = __ldg(&p.chunk_gid[(ret & ~kDetachBit) >> kChunkShift]);
+            const i32 st = vldi(&p.descs[g].status);
+            if (st != 0)
+                atomicCAS(&p.descs[parent].status, 0, st);
+            vst32(&p.descs[g].ret, kEmpty32);
+            fence_acq_rel_gpu();
+            const u64 was = atomicAdd(&p.descs[parent].pe, ~0ull);   // - 1
+            if ((u32)was != 1u) {
+                ret = kEmpty32;
+                g = kEmpty32;   // the parent still runs: nothing completes here
+                break;
+            }
+            g = parent;
+            ret = vld32(&p.descs[g].ret);
+        }
+        if (g == kEmpty32) {
+            // done above
+        } else if (ret != kEmpty32) {
             // a composed graph is done: its module task resumes (a
             // continuation activation) and inherits its status
             const i32 st = vldi(&p.descs[g].status);
@@ -779,13 +800,15 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         // a module task whose composed graph finished: release its successors
         const bool cont = modules && act && kind >= TG_MODULE && (stt.x & kAwait) != 0u;
         const bool enter = modules && act && kind >= TG_MODULE && !cont;
+        // a detached subflow releases its successors at its first step
+        const bool detached = enter && kind == TG_SUBFLOW && (arg & 1u) != 0u;
 
         // Successor ids of static tasks are fetched before the payload runs,
         // so their latency hides under it.  If no lane has more than
         // kPerLaneMax successors each lane releases its own; otherwise the
         // edges are flattened over the warp (edge e belongs to the lane
         // whose exclusive prefix covers it) to spread a wide fan-out.
-        const u32 c = (act && (kind == TG_STATIC || cont)) ? succ_cnt : 0u;
+        const u32 c = (act && (kind == TG_STATIC || cont || detached)) ? succ_cnt : 0u;
         const u32 maxc = __reduce_max_sync(kFull, c);
         const bool per_lane = maxc <= kPerLaneMax;
         if (traced) {
@@ -866,7 +889,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         }
 
         const bool run = act && c_status == 0;
-        const u32 U = run ? ((kind == TG_STATIC || cont) ? succ_cnt : 1u) : 0u;
+        const u32 U = run ? ((kind == TG_STATIC || cont) ? succ_cnt : (detached ? succ_cnt + 1u : 1u)) : 0u;
         // reserve the pending count of every activation this warp may push
         // before any of them becomes visible (a fence precedes publication)
         if (single) {
@@ -1051,7 +1074,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             atomicCAS(&p.descs[racy].status, 0, TG_ERR_RACE);
 
         if (enter && run)
-            mp++;   // a module task's continuation: pushed when its graph completes
+            mp++;   // a module task's continuation, or a detached copy's token of this graph
 
         // ---- release own in-flight flags (with the new count and digest).
         // The fence orders them before the publication of new work; a step
@@ -1064,7 +1087,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             if (run)
                 __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt),
                        make_uint2((cont ? iter : iter + 1u) | (keep_self ? kInflight : 0u) |
-                                      (enter ? (kInflight | kAwait) : 0u),
+                                      ((enter && !detached) ? (kInflight | kAwait) : 0u),
                                   dg));
             if (kServe || ns > kHandMax || any_enter)
                 fence_acq_rel_gpu();
@@ -1089,7 +1112,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 m_n = ld_imm<kServe>(&p.descs[m_g].n);
                 const u64 was = atomicAdd(&p.descs[m_g].pe, (u64)m_nsrc);
                 if ((u32)was == 0u) {
-                    vst32(&p.descs[m_g].ret, u);
+                    vst32(&p.descs[m_g].ret, u | (detached ? kDetachBit : 0u));
                     if (kind == TG_SUBFLOW) {
                         // a fresh copy: no executions, no status, no join value yet
                         vst64(&p.descs[m_g].pe, (u64)m_nsrc);
@@ -1100,6 +1123,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 } else {
                     atomicAdd(&p.descs[m_g].pe, (u64)0 - (u64)m_nsrc);
                     atomicCAS(&p.descs[gid].status, 0, TG_ERR_RACE);
+                    if (detached)
+                        atomicAdd(&p.descs[gid].pe, ~0ull);   // no copy holds the token
                 }
             }
             // a subflow copy's tasks start from their initial state
@@ -1118,7 +1143,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 }
             }
             fence_acq_rel_gpu();
-            emit(w, enter && run && !entered, (u64)u, lane, st_spill);
+            emit(w, enter && run && !entered && !detached, (u64)u, lane, st_spill);
             u32 rem = __ballot_sync(kFull, entered);
             while (rem) {
                 const int l = __ffs(rem) - 1;

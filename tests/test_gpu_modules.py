@@ -247,3 +247,48 @@ def test_composed_graphs_in_a_batch(ex):
     ht.destroy()
     for h in hm:
         h.destroy()
+
+
+def test_detached_subflows(ex):
+    """Detached subflows: successors released at once with the task's output;
+    the launch still waits for every copy (the execution counter includes
+    them); inside a composed graph the module task resumes only after the
+    detached copies of that graph ended; in a batch too."""
+    sub = from_lists("B_subflow", [STATIC] * 3, pack_param([R] * 3), [(0, 2), (1, 2)])
+    big = w.config2a(seed=17, levels=6, width=80, rounds=40)
+    det = from_lists("fig_det", [STATIC, SUBFLOW, SUBFLOW, STATIC],
+                     [pack_param(R), pack_param(R, 0, 1), pack_param(R, 0, 1), pack_param(R)],
+                     [(0, 1), (0, 2), (1, 3), (2, 3)])
+    hs, hb = ex.graph(sub), ex.graph(big)
+    ht = ex.graph(det, modules={1: hs, 2: hb})
+    for _ in range(3):
+        st = ex.run(ht)
+        ref = oc.run({"s": sub, "b": big, "t": det}, {"t": {1: "s", 2: "b"}}, "t")
+        assert st == 0 == ref["t"][0]
+        out, cnt, dig, execs = ex.result(ht)
+        np.testing.assert_array_equal(out, ref["t"][1])
+        np.testing.assert_array_equal(cnt, ref["t"][2])
+        assert ex.stats()["tasks"] == ref["*"]
+    # a module whose graph holds a detached subflow: the module task resumes
+    # only once that copy is done too
+    top = from_lists("outer", [STATIC, MODULE, STATIC], pack_param([R] * 3), [(0, 1), (1, 2)])
+    ho = ex.graph(top, modules={1: ht})
+    assert ex.run(ho) == 0
+    ref = oc.run({"s": sub, "b": big, "t": det, "o": top}, {"o": {1: "t"}, "t": {1: "s", 2: "b"}}, "o")
+    np.testing.assert_array_equal(ex.result(ho)[0], ref["o"][1])
+    assert ex.stats()["tasks"] == ref["*"]
+    # in a batch, beside a plain graph
+    plain = w.config1(levels=3, width=20, trip=2, rounds=8)
+    hp = ex.graph(plain)
+    b = ex.batch([ho, hp])
+    b.launch()
+    st, sts = b.wait()
+    assert st == 0
+    np.testing.assert_array_equal(ex.result(ho)[0], ref["o"][1])
+    assert ex.stats()["tasks"] == ref["*"] + oracle.run(plain).execs
+    b.destroy()
+    hp.destroy()
+    ho.destroy()
+    ht.destroy()
+    hs.destroy()
+    hb.destroy()
