@@ -179,6 +179,8 @@ int tg_graph_create(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const u
 int tg_graph_create_composed(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
                              uint32_t n_edges, const uint32_t *src, const uint32_t *dst,
                              const uint8_t *weak, uint32_t seed, tg_graph *const *modules, tg_graph **out);
+/* TG_ERR_BUSY while instances of g exist, while it is served, composed by
+ * another graph or held by a live batch. */
 int tg_graph_destroy(tg_ctx *ctx, tg_graph *g);
 
 typedef struct {

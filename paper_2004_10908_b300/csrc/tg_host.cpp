@@ -127,6 +127,7 @@ struct tg_graph {
     bool has_geo = false;
     u32 n_mod = 0;                        // module and subflow tasks
     int n_refs = 0;                       // graphs whose module tasks compose this one
+    int n_batches = 0;                    // live batches holding it
 };
 
 struct tg_batch {
@@ -134,6 +135,7 @@ struct tg_batch {
     std::vector<tg_graph *> gs;
     std::vector<tg_graph *> comp;   // graphs its members' module and subflow tasks reach
     bool has_mod = false;
+    bool counted = false;           // its members count it (tg_graph::n_batches)
     u64 lt_off = 0, lt_len = 0;
     u32 max_n = 0, total_src = 0;
     Geometry geo;
@@ -819,6 +821,7 @@ int tg_instance_create(tg_ctx *c, tg_graph *t, tg_graph **out)
     g->ready = nullptr;
     // what belongs to the template alone stays with it
     g->n_refs = 0;
+    g->n_batches = 0;
     g->mods.clear();
     g->sub_insts.clear();
     g->cap_exec = nullptr;
@@ -855,8 +858,8 @@ int tg_graph_destroy(tg_ctx *c, tg_graph *g)
 {
     if (!c || !g || g->ctx != c)
         return TG_ERR_INVALID;
-    if (g->n_inst > 0 || g->serve_ticket != 0 || g->n_refs > 0)
-        return TG_ERR_BUSY;   // instances still use its packed form, it is being served or composed
+    if (g->n_inst > 0 || g->serve_ticket != 0 || g->n_refs > 0 || g->n_batches > 0)
+        return TG_ERR_BUSY;   // instances use its packed form, or it is served, composed or in a batch
     if (g->busy)
         cudaEventSynchronize(g->busy);
     if (g->ready) {
@@ -1487,6 +1490,9 @@ int tg_batch_create(tg_ctx *c, tg_graph *const *gs, uint32_t n, tg_batch **out)
         tg_batch_destroy(c, b);
         return TG_ERR_CUDA;
     }
+    for (tg_graph *g : b->gs)
+        g->n_batches++;
+    b->counted = true;
     *out = b;
     return TG_OK;
 }
@@ -1554,9 +1560,12 @@ int tg_batch_destroy(tg_ctx *c, tg_batch *b)
         return TG_ERR_INVALID;
     if (b->launched)
         cudaEventSynchronize(b->done);
-    for (tg_graph *g : b->gs)
+    for (tg_graph *g : b->gs) {
         if (g->busy == b->done)
             g->busy = nullptr;
+        if (b->counted)
+            g->n_batches--;
+    }
     if (b->exec)
         cudaGraphExecDestroy(b->exec);
     if (b->done)

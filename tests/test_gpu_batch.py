@@ -170,3 +170,18 @@ def test_graph_autotune_keeps_results_and_caches(tmp_path):
         chosen2, ns2 = e.autotune(h, trials=1, cache_path=cache)
         assert chosen2 == chosen and ns2 == ns
         assert len(open(cache).read().splitlines()) == 1
+
+
+def test_graph_in_a_live_batch_cannot_be_destroyed(ex):
+    from paper_2004_10908_b300 import binding as B
+    gs = [w.diamond(), w.do_while(3, 2)]
+    hs = [ex.graph(g) for g in gs]
+    b = ex.batch(hs)
+    assert B.tg_graph_destroy(ex.ctx, hs[0].handle) == B.TG_ERR_BUSY
+    b.launch()
+    st, sts = b.wait()
+    assert st == 0
+    b.destroy()
+    for h in hs:
+        assert B.tg_graph_destroy(ex.ctx, h.handle) == 0
+        h.handle = None
