@@ -8,6 +8,7 @@
 #include <string>
 #include <functional>
 #include <map>
+#include <set>
 #include <new>
 #include <vector>
 
@@ -153,6 +154,8 @@ struct Submission {
 
 struct tg_ctx {
     int device = 0, sm_count = 0;
+    std::set<tg_graph *> live_graphs;   // freed with the context if the caller did not
+    std::set<tg_batch *> live_batches;
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
     tg_ctx_opts opts{};
@@ -537,6 +540,22 @@ int tg_ctx_destroy(tg_ctx *c)
         cudaEventDestroy(c->ev_k0);
     if (c->ev_k1)
         cudaEventDestroy(c->ev_k1);
+    // batches and graphs the caller did not destroy (their device memory is
+    // the caller's arena; only host objects, captured graphs and events)
+    for (tg_batch *b : c->live_batches) {
+        if (b->exec)
+            cudaGraphExecDestroy(b->exec);
+        if (b->done)
+            cudaEventDestroy(b->done);
+        delete b;
+    }
+    for (tg_graph *g : c->live_graphs) {
+        if (g->cap_exec)
+            cudaGraphExecDestroy(g->cap_exec);
+        if (g->ready)
+            cudaEventDestroy(g->ready);
+        delete g;
+    }
     delete c;
     return TG_OK;
 }
@@ -634,6 +653,7 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
         delete g;
         return TG_ERR_BUDGET;
     }
+    c->live_graphs.insert(g);
     g->n_chunks = n_chunks;
     g->node_off = g->chunk_off << kChunkShift;
     // the pristine image starts on a 256-byte boundary (64 entries), so its
@@ -643,6 +663,7 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
     g->edge_len = lead + 64 + 8ull * n;
     if (!c->edge_pool.alloc(g->edge_len, g->edge_off)) {
         c->nodes.release(g->chunk_off, n_chunks);
+        c->live_graphs.erase(g);
         delete g;
         return TG_ERR_BUDGET;
     }
@@ -814,6 +835,7 @@ int tg_instance_create(tg_ctx *c, tg_graph *t, tg_graph **out)
         return TG_ERR_INVALID;
     }
     *g = *src;
+    c->live_graphs.insert(g);
     g->chunk_off = chunk_off;
     g->tmpl = src;
     g->n_inst = 0;
@@ -889,6 +911,7 @@ int tg_graph_destroy(tg_ctx *c, tg_graph *g)
             ++it;
         }
     }
+    c->live_graphs.erase(g);
     delete g;
     return TG_OK;
 }
@@ -1462,10 +1485,12 @@ int tg_batch_create(tg_ctx *c, tg_graph *const *gs, uint32_t n, tg_batch **out)
     tg_batch *b = new (std::nothrow) tg_batch();
     if (!b)
         return TG_ERR_INVALID;
+    c->live_batches.insert(b);
     b->ctx = c;
     b->gs.assign(gs, gs + n);
     b->lt_len = (u64)n * 2;
     if (!c->edge_pool.alloc(b->lt_len, b->lt_off)) {
+        c->live_batches.erase(b);
         delete b;
         return TG_ERR_BUDGET;
     }
@@ -1572,6 +1597,7 @@ int tg_batch_destroy(tg_ctx *c, tg_batch *b)
         cudaEventDestroy(b->done);
     if (b->lt_len)
         c->edge_pool.release(b->lt_off, b->lt_len);
+    c->live_batches.erase(b);
     delete b;
     return TG_OK;
 }

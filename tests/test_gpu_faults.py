@@ -51,3 +51,24 @@ def test_cancel_then_context_still_works():
         gh.destroy()
         dev, ref = run_both(ex, w.do_while())
         assert_same(dev, ref, "after cancel")
+
+
+def test_context_destroy_frees_what_the_caller_left():
+    """Graphs, instances, composed graphs and batches left alive are freed
+    with their context; a new context on the same device works."""
+    from paper_2004_10908_b300 import Executor
+    from workloads.graphs import MODULE, STATIC, from_lists, pack_param
+    for _ in range(3):
+        e = Executor(arena_bytes=1 << 28)
+        g = e.graph(w.config1(levels=3, width=20, trip=2, rounds=4))
+        e.instance(g)
+        inner = e.graph(w.diamond())
+        top = e.graph(from_lists("t", [STATIC, MODULE], pack_param([2, 2]), [(0, 1)]), modules={1: inner})
+        b = e.batch([g, top])
+        b.launch()
+        assert b.wait()[0] == 0
+        e.capture_run(inner, 2)
+        e.close()           # nothing destroyed by hand
+    with Executor(arena_bytes=1 << 28) as e:
+        h = e.graph(w.diamond())
+        assert e.run(h) == 0
