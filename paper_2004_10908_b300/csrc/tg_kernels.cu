@@ -234,7 +234,7 @@ struct WarpCtx {
 };
 
 // Route the new ready activations of the warp (lanes with `has`).
-__device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u64 &spill_ctr)
+__device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u32 &spill_ctr)
 {
     if (__ballot_sync(kFull, has) == 0)
         return;
@@ -333,7 +333,7 @@ __device__ __forceinline__ T ld_imm(const T *ptr)
 
 // Stage the new activations of the lanes with `has` in the warp's buffer;
 // a full buffer is published early (its owners keep their flags meanwhile).
-__device__ __forceinline__ void stage(WarpCtx &w, u64 *buf, u32 &ns, bool has, u64 ent, int lane, u64 &spill_ctr)
+__device__ __forceinline__ void stage(WarpCtx &w, u64 *buf, u32 &ns, bool has, u64 ent, int lane, u32 &spill_ctr)
 {
     const u32 m = __ballot_sync(kFull, has);
     if (m == 0)
@@ -353,7 +353,7 @@ __device__ __forceinline__ void stage(WarpCtx &w, u64 *buf, u32 &ns, bool has, u
     ns += k;
 }
 
-__device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, u64 &spill_ctr)
+__device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, u32 &spill_ctr)
 {
     __syncwarp();
     for (u32 i = 0; i < ns; i += 32u) {
@@ -422,7 +422,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     w.avail_word = &p.ctl->avail[blockIdx.x >> 5];
     w.avail_bit = 1u << (blockIdx.x & 31u);
     // a composed graph's completion resumes its module task: published after a fence
-    auto resume = [&](u64 cont, u64 &spill_ctr) {
+    auto resume = [&](u64 cont, u32 &spill_ctr) {
         if (!modules)
             return;
         const bool h = cont != kEmpty;
@@ -435,8 +435,10 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     u32 *my_keep = s_keep + warp * 32;
     u64 *my_stage = s_ring + ring_n + (size_t)warp * kStage;
 
-    u64 st_tasks = 0, st_local = 0, st_own = 0, st_try = 0, st_hit = 0, st_inj = 0, st_spill = 0,
-        st_idle = 0, st_iters = 0, st_hand = 0, st_park = 0, st_fail = 0;
+    // per-warp counters, 32-bit (registers are scarce); idle loops may exceed 2^32 in a long-lived server
+    u32 st_tasks = 0, st_local = 0, st_own = 0, st_try = 0, st_hit = 0, st_inj = 0, st_spill = 0,
+        st_iters = 0, st_hand = 0, st_park = 0, st_fail = 0;
+    u64 st_idle = 0;
     // adaptive thieves (Alg. 3/6 invariant): a block is active while one of
     // its warps executes; blocks are the workers whose counts are kept
     const bool adaptive = !kServe && kExt && p.thief_mode == 1u;
