@@ -197,7 +197,9 @@ int tg_graph_get_info(const tg_graph *g, tg_graph_info *info);
 int tg_run(tg_ctx *ctx, tg_graph *g);
 
 /* Asynchronous form: enqueue the run and return at once.  *ticket names the
- * submission for tg_poll / tg_wait.  TG_ERR_BUSY if g is still in flight. */
+ * submission for tg_poll / tg_wait; it stays valid until g is submitted
+ * again or destroyed (a new submission of g releases g's earlier tickets).
+ * TG_ERR_BUSY if g is still in flight. */
 int tg_submit(tg_ctx *ctx, tg_graph *g, uint64_t *ticket);
 /* Never blocks: TG_PENDING while the run is in flight, else its status. */
 int tg_poll(tg_ctx *ctx, uint64_t ticket);

@@ -931,6 +931,7 @@ int tg_graph_get_info(const tg_graph *g, tg_graph_info *info)
 }
 
 static int serve_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket);
+static int finish_sub(tg_ctx *c, Submission &s);
 
 // Every graph that the module and subflow tasks of `roots` reach
 // (transitively), the roots themselves excluded.
@@ -962,6 +963,18 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
         return g->n_mod ? TG_ERR_INVALID : serve_submit(c, g, ticket);
     if (graph_busy(g))
         return TG_ERR_BUSY;
+    // the graph's earlier submissions have finished: take their statuses (a
+    // failed run marks the queues for clearing) and release their tickets
+    for (auto it = c->subs.begin(); it != c->subs.end();) {
+        if (it->second.g == g) {
+            finish_sub(c, it->second);
+            if (it->second.ev)
+                cudaEventDestroy(it->second.ev);
+            it = c->subs.erase(it);
+        } else {
+            ++it;
+        }
+    }
     int rc = clear_if_dirty(c);
     if (rc != TG_OK)
         return rc;

@@ -1354,10 +1354,15 @@ __global__ void module_rearm_kernel(KParams p, u32 gid, u32 n)
 }
 
 // After the scheduler: unfinished graphs take the launch's abort code; every
-// status is mirrored to host-mapped memory.
+// status is mirrored to host-mapped memory.  An aborted launch (time limit,
+// cancel, internal error) may leave activations in its queues; they are
+// emptied here, so that the next launch on the stream starts from empty
+// slots whether or not the host has seen this launch's status yet.
 __global__ void finalize_kernel(KParams p)
 {
-    for (u32 gi = blockIdx.x * blockDim.x + threadIdx.x; gi < p.n_graphs; gi += gridDim.x * blockDim.x) {
+    const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 nthreads = gridDim.x * blockDim.x;
+    for (u32 gi = tid; gi < p.n_graphs; gi += nthreads) {
         const u32 gid = p.lt ? p.lt[gi].gid : p.single_gid;
         GDesc &D = p.descs[gid];
         i32 st = D.status;
@@ -1368,6 +1373,13 @@ __global__ void finalize_kernel(KParams p)
         }
         if (p.status_out)
             p.status_out[gid] = st;
+    }
+    if (p.ctl->abort_code != 0) {
+        for (size_t i = tid; i <= (size_t)p.inj_mask; i += nthreads)
+            p.inj[i] = kEmpty;
+        const size_t dq_slots = (size_t)p.nblocks * p.dq_stride;
+        for (size_t i = tid; i < dq_slots; i += nthreads)
+            p.dq[i] = kEmpty;
     }
 }
 

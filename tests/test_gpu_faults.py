@@ -53,6 +53,37 @@ def test_cancel_then_context_still_works():
         assert_same(dev, ref, "after cancel")
 
 
+def _wide_forever(width=3000):
+    # source -> head -> `width` tasks -> a condition that always jumps back
+    # to the head: at any moment many activations sit in the queues
+    n = width + 3
+    kinds = [0] * (width + 2) + [w.COND_CONST]
+    params = [w.pack_param(32)] * (width + 2) + [w.pack_param(4, 0, 0)]
+    edges = [(0, 1)] + [(1, 2 + i) for i in range(width)] + [(2 + i, n - 1) for i in range(width)] + [(n - 1, 1)]
+    return w.from_lists("wide_forever", kinds, params, edges)
+
+
+def test_aborted_launch_leaves_clean_queues_for_the_next_submission():
+    """A launch that hits its time limit with activations still queued, and
+    another graph submitted behind it before the host has read the first
+    status: the second run must match the oracle (the aborted launch's
+    queues are emptied on the device before the next launch starts)."""
+    from paper_2004_10908_b300 import Executor, binding as B
+    g_ok = w.config2a(seed=4, levels=40, width=400, rounds=8)
+    ref = oracle.run(g_ok)
+    with Executor(arena_bytes=512 << 20, time_limit_ns=50_000_000) as ex:
+        ga = ex.graph(_wide_forever())
+        gb = ex.graph(g_ok)
+        for _ in range(3):
+            ta = ex.submit(ga)
+            tb = ex.submit(gb)
+            assert ex.wait(ta) == B.TG_ERR_TIMEOUT
+            st = ex.wait(tb)
+            assert_same((st,) + tuple(ex.result(gb)), ref, "behind an aborted launch")
+        ga.destroy()
+        gb.destroy()
+
+
 def test_context_destroy_frees_what_the_caller_left():
     """Graphs, instances, composed graphs and batches left alive are freed
     with their context; a new context on the same device works."""
