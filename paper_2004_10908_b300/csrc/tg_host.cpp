@@ -137,6 +137,7 @@ struct tg_batch {
     std::vector<tg_graph *> comp;   // graphs its members' module and subflow tasks reach
     bool has_mod = false;
     bool counted = false;           // its members count it (tg_graph::n_batches)
+    bool acyclic = false;           // no member has condition, module or subflow tasks
     u64 lt_off = 0, lt_len = 0;
     u32 max_n = 0, total_src = 0;
     Geometry geo;
@@ -235,7 +236,7 @@ KParams base_params(tg_ctx *c, const Geometry &g)
     p.dq_mask = g.depth - 1u;
     p.dq_stride = c->dq_cap;
     p.smem_mask = g.ring - 1u;
-    p.flags = c->opts.flags;
+    p.flags = c->opts.flags & ~kFlagAcyclic;
     p.max_steal = g.max_steal;
     p.steal_policy = g.policy;
     p.node_cap = (u32)c->node_cap;
@@ -993,6 +994,8 @@ int tg_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     p.single_gid = g->gid;
     p.max_n = g->n;
     p.total_sources = g->n_src;
+    if (g->n_cond == 0 && g->n_mod == 0)
+        p.flags |= kFlagAcyclic;
     if (g->n_mod) {
         // every graph the composition reaches starts idle from its initial state
         p.has_modules = 1u;
@@ -1445,6 +1448,8 @@ static int batch_capture(tg_ctx *c, tg_batch *b)
     p.max_n = b->max_n;
     p.total_sources = b->total_src;
     p.has_modules = b->has_mod ? 1u : 0u;
+    if (b->acyclic)
+        p.flags |= kFlagAcyclic;
     b->kp = p;
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
@@ -1515,8 +1520,11 @@ int tg_batch_create(tg_ctx *c, tg_graph *const *gs, uint32_t n, tg_batch **out)
     b->max_n = max_n;
     b->total_src = (u32)inj;
     b->geo = c->geo;
-    for (tg_graph *g : b->gs)
+    b->acyclic = true;
+    for (tg_graph *g : b->gs) {
         b->has_mod = b->has_mod || g->n_mod != 0;
+        b->acyclic = b->acyclic && g->n_cond == 0 && g->n_mod == 0;
+    }
     if (b->has_mod)
         b->comp = composition_closure(b->gs);
     int rc = batch_capture(c, b);

@@ -109,6 +109,9 @@ constexpr u32 kAwait = 0x40000000u;       // in NodeSlot::cnt: a module task wai
 constexpr u32 kDetachBit = 0x80000000u;   // in GDesc::ret: the copy of a detached subflow (holds a
                                           // token of its parent graph's pending count)
 constexpr u32 kMaxNodeIndex = 0x7FFFFFFEu;
+constexpr u32 kFlagAcyclic = 0x80000000u;  // in KParams::flags (set by the library, never by the
+                                           // caller): no graph of the launch has condition,
+                                           // module or subflow tasks, so every task runs once
 constexpr u32 kSoleBit = 0x80000000u;     // in a static task's successor id: the target has
                                           // strong in-degree 1 (its join word is never used)
 constexpr u32 kChunkShift = 8;            // node ranges are allocated in 256-task chunks

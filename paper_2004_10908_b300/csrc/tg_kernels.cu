@@ -125,6 +125,15 @@ __device__ __forceinline__ u32 lanemask_lt(int lane) { return (1u << lane) - 1u;
 // (outputs, state, flag releases) before its later publishing writes.  A
 // sequentially consistent fence is not needed and costs far more.
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// The same at block scope: enough when the only readers of what follows are
+// warps of this block (its shared-memory ring), and far cheaper.
+__device__ __forceinline__ void fence_acq_rel_cta() { asm volatile("fence.acq_rel.cta;" ::: "memory"); }
+__device__ __forceinline__ u64 ld_acquire_cta64(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.acquire.cta.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // ---------------------------------------------------------------------------
 // multi-producer multi-consumer rings (shared or global memory)
@@ -137,7 +146,10 @@ struct Ring {
 };
 
 // Warp-cooperative pop into lanes [0, k).  A thief takes half of what it
-// sees (at least one); an owner takes up to 32.
+// sees (at least one); an owner takes up to 32.  A pop from the block's
+// shared-memory ring (kLocal) reads each slot with block-scope acquire: its
+// producer published it after a block-scope release fence.
+template <bool kLocal = false>
 __device__ __forceinline__ int ring_pop(const Ring &r, bool thief, int lane, u64 &e, int &err, int want = 32)
 {
     u32 h = 0;
@@ -161,14 +173,14 @@ __device__ __forceinline__ int ring_pop(const Ring &r, bool thief, int lane, u64
     e = kEmpty;
     if (lane < k) {
         u64 *s = r.slots + ((h + (u32)lane) & r.mask);
-        u64 v = vld64(s);
+        u64 v = kLocal ? ld_acquire_cta64(s) : vld64(s);
         int spins = 0;
         while ((u32)v == kEmpty32) {   // reserved by its producer, not yet written
             if (++spins > kSpinLimit) {
                 err = 1;
                 break;
             }
-            v = vld64(s);
+            v = kLocal ? ld_acquire_cta64(s) : vld64(s);
         }
         if ((u32)v != kEmpty32)
             vst64(s, kEmpty);
@@ -251,6 +263,9 @@ __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u3
     if (!ring_push(w.local, loc, ent, lane, w.err))
         pub = pub || loc;
     if (__ballot_sync(kFull, pub) != 0) {
+        // work leaving the block: what precedes it is made visible GPU-wide
+        // (the block's own ring needed only a block-scope fence)
+        fence_acq_rel_gpu();
         if (lane == 0)
             spill_ctr++;
         if (ring_push(w.own, pub, ent, lane, w.err)) {
@@ -340,6 +355,7 @@ __device__ __forceinline__ void stage(WarpCtx &w, u64 *buf, u32 &ns, bool has, u
         return;
     const u32 k = (u32)__popc(m);
     if (ns + k > kStage) {
+        fence_acq_rel_cta();   // the pending-count reservation first
         __syncwarp();
         for (u32 i = 0; i < ns; i += 32u) {
             const bool h = i + (u32)lane < ns;
@@ -396,7 +412,13 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     }
     __syncthreads();
 
-    const bool race_check = (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
+    // A launch whose graphs have no condition tasks (and compose nothing)
+    // runs every task exactly once: no activation can find its target in
+    // flight, so the in-flight flags -- one returning atomic per released
+    // successor -- are skipped, and the task's own state is stored without a
+    // fence of its own.
+    const bool acyclic = !kServe && (p.flags & kFlagAcyclic) != 0u;
+    const bool race_check = !acyclic && (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
     const int bmax = (int)min(32u, max(1u, p.batch_max));
     // one graph: every activation has gid == single_gid (not when it composes others)
     // kOne: a lean launch of one graph (no launch table); every activation
@@ -480,7 +502,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             nh = 0;
             st_hand++;
         } else {
-            k = ring_pop(w.local, false, lane, e, w.err, bmax);
+            k = ring_pop<true>(w.local, false, lane, e, w.err, bmax);
             if (k) {
                 st_local++;
             } else {
@@ -586,7 +608,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                             emit(w, h, ent, lane, st_spill);
                         }
                         st_inj++;
-                        k = ring_pop(w.local, false, lane, e, w.err, bmax);
+                        k = ring_pop<true>(w.local, false, lane, e, w.err, bmax);
                     }
                 }
                 if (k == 0)
@@ -773,7 +795,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         u32 gid = 0;
         if (act) {
             imm = ld_imm<kServe>(reinterpret_cast<const uint4 *>(&p.slots[u]));
-            stt = __ldcg(reinterpret_cast<const uint2 *>(&p.slots[u].cnt));
+            // (an acyclic launch runs each task once: its count and digest are 0)
+            stt = acyclic ? make_uint2(0u, 0u) : __ldcg(reinterpret_cast<const uint2 *>(&p.slots[u].cnt));
             gid = single ? p.single_gid : ld_imm<kServe>(&p.chunk_gid[u >> kChunkShift]);
         }
         if (act) {
@@ -913,7 +936,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         }
         if (run && !cont)
             st_tasks++;
-        if (!race_check) {
+        if (!race_check && !acyclic) {
             // without in-flight flags the state must be visible before any
             // release makes a later activation of this task possible
             if (run)
@@ -1079,20 +1102,26 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             mp++;   // a module task's continuation, or a detached copy's token of this graph
 
         // ---- release own in-flight flags (with the new count and digest).
-        // The fence orders them before the publication of new work; a step
-        // that publishes nothing (it keeps its output in hand) leaves it to
-        // the next step that does.  The server always fences: the host reads
-        // its completion records while it runs.  A module task keeps its flag
-        // (and marks itself waiting) until its continuation has run.
+        // The fence orders them, and the pending-count reservation, before
+        // the publication of new work; a step that publishes nothing (it
+        // keeps its output in hand) leaves it to the next step that does.
+        // New work goes to the block's shared-memory ring, so a block-scope
+        // fence suffices; activations that leave the block are fenced
+        // GPU-wide where they are pushed (emit).  The server always fences
+        // GPU-wide: the host reads its completion records while it runs.  A
+        // module task keeps its flag (and marks itself waiting) until its
+        // continuation has run.
         const bool any_enter = modules && __any_sync(kFull, (enter && run) || sink_acc);
-        if (race_check) {
+        if (race_check || acyclic) {
             if (run)
                 __stcg(reinterpret_cast<uint2 *>(&p.slots[u].cnt),
                        make_uint2((cont ? iter : iter + 1u) | (keep_self ? kInflight : 0u) |
                                       ((enter && !detached) ? (kInflight | kAwait) : 0u),
                                   dg));
-            if (kServe || ns > kHandMax || any_enter)
+            if (kServe || any_enter)
                 fence_acq_rel_gpu();
+            else if (ns > kHandMax)
+                fence_acq_rel_cta();
         } else if (any_enter) {
             fence_acq_rel_gpu();
         }
@@ -1296,6 +1325,15 @@ __global__ void rearm_kernel(KParams p)
         p.slots[u].W = (u64)(deg >> 16);
         *reinterpret_cast<uint2 *>(&p.slots[u].cnt) = make_uint2(0u, 0u);
         p.outv[u] = 0u;
+    }
+    // the successor lists of this block's tasks are pulled into L2 ahead of
+    // the scheduler, which reads each once, on its critical path
+    if (first < n) {
+        const u32 last = min(n, first + 1024u);
+        const u32 lo = p.slots[off + first].succ_off;
+        const u32 hi = last < n ? p.slots[off + last].succ_off : D.src_off;
+        for (u32 w = (lo & ~31u) + threadIdx.x * 32u; w < hi; w += blockDim.x * 32u)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p.edges + w));
     }
     if (blockIdx.x == 0) {
         for (u32 s = threadIdx.x; s < D.n_src; s += blockDim.x)
