@@ -128,12 +128,40 @@ __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_re
 // The same at block scope: enough when the only readers of what follows are
 // warps of this block (its shared-memory ring), and far cheaper.
 __device__ __forceinline__ void fence_acq_rel_cta() { asm volatile("fence.acq_rel.cta;" ::: "memory"); }
-__device__ __forceinline__ u64 ld_acquire_cta64(const u64 *p)
+
+// Shared-memory forms of the ring accesses (block scope): the block's own
+// ring is only ever touched by the block's warps.
+__device__ __forceinline__ u32 sh_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ u32 lds32(const u32 *p)
 {
-    u64 v;
-    asm volatile("ld.acquire.cta.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    u32 v;
+    asm volatile("ld.relaxed.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"(sh_addr(p)) : "memory");
     return v;
 }
+__device__ __forceinline__ u64 lds64_acq(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.acquire.cta.shared.u64 %0, [%1];" : "=l"(v) : "r"(sh_addr(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ u64 lds64(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.relaxed.cta.shared.u64 %0, [%1];" : "=l"(v) : "r"(sh_addr(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts64(u64 *p, u64 v)
+{
+    asm volatile("st.relaxed.cta.shared.u64 [%0], %1;" ::"r"(sh_addr(p)), "l"(v) : "memory");
+}
+__device__ __forceinline__ u32 cas_s32(u32 *p, u32 cmp, u32 val)
+{
+    u32 old;
+    asm volatile("atom.relaxed.cta.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "r"(sh_addr(p)), "r"(cmp), "r"(val) : "memory");
+    return old;
+}
+template <bool kLocal> __device__ __forceinline__ u32 rld32(const u32 *p) { return kLocal ? lds32(p) : vld32(p); }
+template <bool kLocal> __device__ __forceinline__ u32 rcas32(u32 *p, u32 c, u32 v) { return kLocal ? cas_s32(p, c, v) : atomicCAS(p, c, v); }
 
 // ---------------------------------------------------------------------------
 // multi-producer multi-consumer rings (shared or global memory)
@@ -156,12 +184,12 @@ __device__ __forceinline__ int ring_pop(const Ring &r, bool thief, int lane, u64
     int k = 0;
     if (lane == 0) {
         for (int t = 0; t < kCasTries; ++t) {
-            u32 hh = vld32(r.head), tt = vld32(r.tail);
+            u32 hh = rld32<kLocal>(r.head), tt = rld32<kLocal>(r.tail);
             int avail = (int)(tt - hh);
             if (avail <= 0)
                 break;
             int kk = thief ? min(want, (avail + 1) >> 1) : min(want, avail);
-            if (atomicCAS(r.head, hh, hh + (u32)kk) == hh) {
+            if (rcas32<kLocal>(r.head, hh, hh + (u32)kk) == hh) {
                 h = hh;
                 k = kk;
                 break;
@@ -173,23 +201,28 @@ __device__ __forceinline__ int ring_pop(const Ring &r, bool thief, int lane, u64
     e = kEmpty;
     if (lane < k) {
         u64 *s = r.slots + ((h + (u32)lane) & r.mask);
-        u64 v = kLocal ? ld_acquire_cta64(s) : vld64(s);
+        u64 v = kLocal ? lds64_acq(s) : vld64(s);
         int spins = 0;
         while ((u32)v == kEmpty32) {   // reserved by its producer, not yet written
             if (++spins > kSpinLimit) {
                 err = 1;
                 break;
             }
-            v = kLocal ? ld_acquire_cta64(s) : vld64(s);
+            v = kLocal ? lds64_acq(s) : vld64(s);
         }
-        if ((u32)v != kEmpty32)
-            vst64(s, kEmpty);
+        if ((u32)v != kEmpty32) {
+            if (kLocal)
+                sts64(s, kEmpty);
+            else
+                vst64(s, kEmpty);
+        }
         e = v;
     }
     return k;
 }
 
 // Warp-cooperative push of the lanes with `has`; all or nothing.
+template <bool kLocal = false>
 __device__ __forceinline__ bool ring_push(const Ring &r, bool has, u64 ent, int lane, int &err)
 {
     u32 m = __ballot_sync(kFull, has);
@@ -200,10 +233,10 @@ __device__ __forceinline__ bool ring_push(const Ring &r, bool has, u64 ent, int 
     int ok = 0;
     if (lane == 0) {
         for (int tr = 0; tr < kCasTries; ++tr) {
-            u32 tt = vld32(r.tail), hh = vld32(r.head);
+            u32 tt = rld32<kLocal>(r.tail), hh = rld32<kLocal>(r.head);
             if ((int)(tt + (u32)k - hh) > (int)(r.mask + 1u))
                 break;   // full
-            if (atomicCAS(r.tail, tt, tt + (u32)k) == tt) {
+            if (rcas32<kLocal>(r.tail, tt, tt + (u32)k) == tt) {
                 t = tt;
                 ok = 1;
                 break;
@@ -217,18 +250,22 @@ __device__ __forceinline__ bool ring_push(const Ring &r, bool has, u64 ent, int 
     if (has) {
         u64 *s = r.slots + ((t + (u32)__popc(m & lanemask_lt(lane))) & r.mask);
         int spins = 0;
-        while ((u32)vld64(s) != kEmpty32) {   // previous occupant not yet taken
+        while ((u32)(kLocal ? lds64(s) : vld64(s)) != kEmpty32) {   // previous occupant not yet taken
             if (++spins > kSpinLimit) {
                 err = 1;
                 break;
             }
         }
-        vst64(s, ent);
+        if (kLocal)
+            sts64(s, ent);
+        else
+            vst64(s, ent);
     }
     return true;
 }
 
-__device__ __forceinline__ u32 ring_size(const Ring &r) { return vld32(r.tail) - vld32(r.head); }
+template <bool kLocal = false>
+__device__ __forceinline__ u32 ring_size(const Ring &r) { return rld32<kLocal>(r.tail) - rld32<kLocal>(r.head); }
 
 // ---------------------------------------------------------------------------
 // the persistent scheduler
@@ -254,13 +291,13 @@ __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u3
     // one otherwise (the hungry count is read only past the short mark)
     int spill = 0;
     if (lane == 0) {
-        const u32 lsz = ring_size(w.local);
+        const u32 lsz = ring_size<true>(w.local);
         spill = lsz >= w.keep_hi || (lsz >= w.high_water && (i32)vld32(w.hungry) > 0);
     }
     spill = __shfl_sync(kFull, spill, 0);
     bool pub = has && spill;
     bool loc = has && !pub;
-    if (!ring_push(w.local, loc, ent, lane, w.err))
+    if (!ring_push<true>(w.local, loc, ent, lane, w.err))
         pub = pub || loc;
     if (__ballot_sync(kFull, pub) != 0) {
         // work leaving the block: what precedes it is made visible GPU-wide
