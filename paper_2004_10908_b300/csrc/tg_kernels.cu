@@ -553,7 +553,9 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 // (Alg. 6/7), and at most max_thieves blocks steal at once; only
                 // thieves poll launch-wide state, the other idle warps wait on
                 // shared memory, so idle polling never floods L2.
-                if (*(volatile int *)&s_stop)
+                // leave together: a warp whose lanes split here would wait
+                // forever in its next warp-wide operation
+                if (__any_sync(kFull, *(volatile int *)&s_stop != 0))
                     break;
                 int am = 0;
                 if (lane == 0) {
@@ -1284,7 +1286,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             }
         }
         mark(4);
-        if (w.err) {
+        // a bounded wait that gave up (any lane): the whole warp stops
+        if (__any_sync(kFull, w.err != 0)) {
             if (lane == 0)
                 atomicCAS(&p.ctl->abort_code, 0, TG_ERR_INTERNAL);
             break;
