@@ -17,10 +17,11 @@
 // 32-bit tickets and an EMPTY marker per slot; every wait is bounded.
 // Module tasks run another graph to completion and resume as a continuation
 // (Composable Tasking); subflow tasks do the same on a fresh copy of a
-// template (Dynamic Tasking).  The scheduler comes in four compiled
-// variants: lean one-shot kernels for one graph and for batches, an
-// extended one-shot kernel with the optional features (module and subflow
-// tasks, adaptive thieves, tracing), and the resident server.
+// template (Dynamic Tasking).  The scheduler comes in five compiled
+// variants: lean one-shot kernels for one graph, for one graph without
+// condition tasks, and for batches, an extended one-shot kernel with the
+// optional features (module and subflow tasks, adaptive thieves, tracing),
+// and the resident server.
 #include <mutex>
 
 #include "tg_internal.h"
@@ -419,7 +420,7 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
 // or subflow tasks, the adaptive thief mode or tracing -- which lives in a
 // separate variant, so that other launches carry none of that code (it costs
 // them 5-19 % per dependency hop, measured).
-template <bool kServe, bool kExt, bool kOne>
+template <bool kServe, bool kExt, bool kOne, bool kAcyc = false>
 __device__ __forceinline__ void sched_body(const KParams &p)
 {
     extern __shared__ u64 s_ring[];
@@ -454,7 +455,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     // flight, so the in-flight flags -- one returning atomic per released
     // successor -- are skipped, and the task's own state is stored without a
     // fence of its own.
-    const bool acyclic = !kServe && (p.flags & kFlagAcyclic) != 0u;
+    // (kAcyc: the same known at compile time, every task is a static one)
+    const bool acyclic = kAcyc || (!kServe && (p.flags & kFlagAcyclic) != 0u);
     const bool race_check = !acyclic && (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
     const int bmax = (int)min(32u, max(1u, p.batch_max));
     // one graph: every activation has gid == single_gid (not when it composes others)
@@ -857,7 +859,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         const u32 succ_cnt = imm.y & 0xFFFFu;
         const u32 indeg = imm.y >> 16;
         const u32 rounds = imm.z & 0xFFFFu;
-        const u32 kind = (imm.z >> 16) & 0xFFu;
+        const u32 kind = kAcyc ? (u32)TG_STATIC : ((imm.z >> 16) & 0xFFu);
         const u32 arg = imm.z >> 24;
         const u32 lid = imm.w;
         const u32 iter = stt.x & ~(kInflight | kAwait);
@@ -932,8 +934,9 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         resume(settle_finish<kServe, kExt>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
 
         // a strong activation consumed its join word: re-arm it for the next
-        // round (composes with releases of that round that arrive early)
-        if (act && strong)
+        // round (composes with releases of that round that arrive early); a
+        // task of an acyclic launch has no next round
+        if (act && strong && !acyclic)
             atomicAdd(&p.slots[u].W, (u64)indeg - ((u64)insum << 32));
 
         if (kExt && p.trace && act)
@@ -1144,12 +1147,15 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         // The fence orders them, and the pending-count reservation, before
         // the publication of new work; a step that publishes nothing (it
         // keeps its output in hand) leaves it to the next step that does.
-        // New work goes to the block's shared-memory ring, so a block-scope
-        // fence suffices; activations that leave the block are fenced
-        // GPU-wide where they are pushed (emit).  The server always fences
-        // GPU-wide: the host reads its completion records while it runs.  A
-        // module task keeps its flag (and marks itself waiting) until its
-        // continuation has run.
+        // The flag release must reach L2 before any later activation of the
+        // task can test it there (an atomic, which a block-scope fence does
+        // not order against a plain store): GPU scope.  An acyclic launch
+        // has no flags and its tasks run once, so there the only ordering
+        // is the reservation's, for the block's own ring: block scope
+        // (activations that leave the block are fenced GPU-wide where they
+        // are pushed, in emit).  The server always fences GPU-wide: the host
+        // reads its completion records while it runs.  A module task keeps
+        // its flag (and marks itself waiting) until its continuation has run.
         const bool any_enter = modules && __any_sync(kFull, (enter && run) || sink_acc);
         if (race_check || acyclic) {
             if (run)
@@ -1157,7 +1163,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                        make_uint2((cont ? iter : iter + 1u) | (keep_self ? kInflight : 0u) |
                                       ((enter && !detached) ? (kInflight | kAwait) : 0u),
                                   dg));
-            if (kServe || any_enter)
+            if (kServe || any_enter || (ns > kHandMax && !acyclic))
                 fence_acq_rel_gpu();
             else if (ns > kHandMax)
                 fence_acq_rel_cta();
@@ -1333,11 +1339,12 @@ __device__ __forceinline__ void sched_body(const KParams &p)
 }
 
 // One-shot launches (single graphs, batches): at most 512 threads (16 worker
-// warps), so that 128 registers per thread fill the SM.  kOne: one graph.
-template <bool kExt, bool kOne>
+// warps), so that 128 registers per thread fill the SM.  kOne: one graph;
+// kAcyc: one graph without condition tasks (every task static, run once).
+template <bool kExt, bool kOne, bool kAcyc = false>
 __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
 {
-    sched_body<false, kExt, kOne>(p);
+    sched_body<false, kExt, kOne, kAcyc>(p);
 }
 
 // The resident server (its blocks are at most half an SM).
@@ -1557,6 +1564,9 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
             e = cudaFuncSetAttribute(sched_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
+            e = cudaFuncSetAttribute(sched_kernel<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+            if (e != cudaSuccess)
+                return e;
             e = cudaFuncSetAttribute(sched_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
@@ -1572,16 +1582,19 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
     if (serve)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, serve_kernel, threads, dyn_smem);
     // the extended variant must fit the same block shape
-    int ext = 0, one = 0;
+    int ext = 0, one = 0, acyc = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ext, sched_kernel<true, false>, threads, dyn_smem);
     if (e != cudaSuccess)
         return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&one, sched_kernel<false, true>, threads, dyn_smem);
     if (e != cudaSuccess)
         return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&acyc, sched_kernel<false, true, true>, threads, dyn_smem);
+    if (e != cudaSuccess)
+        return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false, false>, threads, dyn_smem);
     if (e == cudaSuccess)
-        *blocks_per_sm = std::min(*blocks_per_sm, std::min(ext, one));
+        *blocks_per_sm = std::min(*blocks_per_sm, std::min(ext, std::min(one, acyc)));
     return e;
 }
 
@@ -1609,6 +1622,8 @@ cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t
     else
         if (p.has_modules || p.thief_mode == 1u || p.trace != nullptr)
             sched_kernel<true, false><<<blocks, threads, smem, st>>>(p);
+        else if (p.lt == nullptr && (p.flags & kFlagAcyclic) != 0u)
+            sched_kernel<false, true, true><<<blocks, threads, smem, st>>>(p);
         else if (p.lt == nullptr)
             sched_kernel<false, true><<<blocks, threads, smem, st>>>(p);
         else
