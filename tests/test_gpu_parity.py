@@ -274,3 +274,23 @@ def test_tracing_keeps_results_and_records_times():
         ran = ref.cnt > 0
         assert (t0[ran] > 0).all() and (t1[ran] >= t0[ran]).all()
         gh.destroy()
+
+
+def test_looping_graphs_never_report_a_false_race():
+    """Graphs whose conditions loop back (a task re-activated soon after its
+    own step, often by a sibling warp of the same block) run many times at
+    several launch shapes: every run must be OK and equal the oracle -- the
+    in-flight flag a task clears must be visible to the flag test of its
+    next activation."""
+    from paper_2004_10908_b300 import Executor
+    graphs = [w.config1(levels=6, width=60, trip=3, rounds=16), w.do_while(300, 2),
+              w.config3(seed=4, n_cond=80, body_levels=3, body_width=5, rounds=4, trip_max=6)] + \
+             [w.nested_loops(s) for s in range(3)]
+    refs = [oracle.run(g) for g in graphs]
+    for geo in (dict(), dict(warps_per_block=4, worker_blocks=592), dict(warps_per_block=8, batch_max=8)):
+        with Executor(arena_bytes=1 << 29, **geo) as ex:
+            hs = [ex.graph(g) for g in graphs]
+            for _ in range(8):
+                for g, h, ref in zip(graphs, hs, refs):
+                    st = ex.run(h)
+                    assert_same((st,) + tuple(ex.result(h)), ref, f"{g.name} {geo}")
