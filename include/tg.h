@@ -100,7 +100,9 @@ enum {
 };
 
 /* Option flags. */
-#define TG_OPT_NO_RACE_CHECK 0x1u   /* skip the per-activation in-flight check */
+#define TG_OPT_NO_RACE_CHECK 0x1u   /* skip the per-activation in-flight check (launches whose
+                                       graphs have no condition, module or subflow tasks skip it
+                                       anyway: every task runs once, a race cannot occur) */
 #define TG_OPT_TRACE 0x2u           /* record per-task start / publish times (tg_trace_copy) and
                                        per-phase cycle counts, in single-graph and batch launches
                                        (not in the resident server) */
