@@ -271,9 +271,9 @@ def e2e(ex, graphs, reps):
             assert ex.run(gh) == 0
             ex.result(gh)
             # copied per graph: successor lists + sources + record image, chunk
-            # table, descriptor; back: outputs and the 32-byte records
+            # table, descriptor; back: outputs and the packed count/digest words
             h2d += g.m * 4 + g.n * 4 + 32 * g.n + 64 + ((g.n + 255) // 256) * 4
-            d2h += g.n * 4 + g.n * 32
+            d2h += g.n * 4 + g.n * 8
             gh.destroy()
         ms.append(1000 * (time.perf_counter() - t0))
     return statistics.mean(ms), h2d, d2h

@@ -173,5 +173,7 @@ cudaError_t launch_bench_payload(u64 count, u32 rounds, u32 *checksum, cudaStrea
 cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink, cudaStream_t st);
 cudaError_t launch_bench_chain(u32 hops, u32 rounds, u32 *last, cudaStream_t st);
 cudaError_t launch_capture_task(NodeSlot *slots, u32 *outv, const u32 *edges, u32 u, u32 node_off, cudaStream_t st);
+// tg_result.cu: pack the count and digest of tasks [node_off, node_off + n) into dst[0, n)
+cudaError_t launch_result_gather(const NodeSlot *slots, u32 node_off, u32 n, u64 *dst, cudaStream_t st);
 
 }  // namespace tg
