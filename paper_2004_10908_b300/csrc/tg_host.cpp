@@ -623,30 +623,30 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
         n_cond += is_cond(kinds[v]);
         n_mod += kinds[v] >= TG_MODULE;
     }
-    for (u32 e = 0; e < m; ++e)
-        if (src[e] >= n || dst[e] >= n)
-            return TG_ERR_INVALID;
+    // degrees, with each edge's endpoints checked before they are used
     std::vector<u32> outdeg(n, 0), sin(n, 0), win(n, 0);
     for (u32 e = 0; e < m; ++e) {
-        outdeg[src[e]]++;
-        if (!is_cond(kinds[src[e]]))
-            sin[dst[e]]++;
+        const u32 sv = src[e], dv = dst[e];
+        if (sv >= n || dv >= n)
+            return TG_ERR_INVALID;
+        outdeg[sv]++;
+        if (!is_cond(kinds[sv]))
+            sin[dv]++;
         else
-            win[dst[e]]++;
+            win[dv]++;
     }
+    u32 n_src = 0;
     for (u32 v = 0; v < n; ++v) {
         if (is_cond(kinds[v]) && outdeg[v] == 0)
             return TG_ERR_INVALID;
         if (outdeg[v] > kMaxDegree || sin[v] > kMaxDegree)
             return TG_ERR_INVALID;
+        n_src += (sin[v] == 0 && win[v] == 0);
     }
     if (weak)
         for (u32 e = 0; e < m; ++e)
             if ((weak[e] != 0) != is_cond(kinds[src[e]]))
                 return TG_ERR_EDGE_KIND;
-    u32 n_src = 0;
-    for (u32 v = 0; v < n; ++v)
-        n_src += (sin[v] == 0 && win[v] == 0);
     if (n_src == 0)
         return TG_ERR_NO_SOURCE;
 
