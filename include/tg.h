@@ -156,7 +156,9 @@ int tg_ctx_destroy(tg_ctx *ctx);
  * without successors, loop trip 0, out-degree or strong in-degree > 65535,
  * n == 0), then TG_ERR_EDGE_KIND, then TG_ERR_NO_SOURCE; TG_ERR_BUDGET if
  * the pools cannot hold it.  Packing: successors in insertion order, 32-byte
- * node records, strong in-degree per task, the source list. */
+ * node records, strong in-degree per task, the source list.  The upload uses
+ * the context's side stream and is complete when the call returns; a graph
+ * may be created while other graphs run on the context stream. */
 int tg_graph_create(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
                     uint32_t n_edges, const uint32_t *src, const uint32_t *dst,
                     const uint8_t *weak, uint32_t seed, tg_graph **out);

@@ -268,7 +268,8 @@ int ensure_stage(tg_ctx *c, size_t bytes)
     if (c->stage_bytes >= bytes)
         return TG_OK;
     if (c->h_stage) {
-        cudaStreamSynchronize(c->stream);
+        cudaStreamSynchronize(c->stream);   // read-backs
+        cudaStreamSynchronize(c->side);     // graph uploads
         cudaFreeHost(c->h_stage);
         c->h_stage = nullptr;
         c->stage_bytes = 0;
@@ -710,7 +711,7 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
                 }
                 g->sub_insts.push_back(inst);
             }
-    cudaStreamSynchronize(c->stream);   // staging buffer may still feed an earlier copy
+    cudaStreamSynchronize(c->side);   // the staging buffer may still feed an earlier upload
     // the staging image starts at the same offset within 256 bytes as its
     // device copy, so the records start on a 256-byte boundary here too
     char *stage = c->h_stage + (g->edge_off & 63u) * 4u;
@@ -787,13 +788,18 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
     _mm_sfence();   // the streamed records are in memory before the copy engine reads them
 #endif
     memcpy(stage + edge_bytes + chunk_bytes, &d, sizeof(d));
-    cudaError_t e1 = cudaMemcpyAsync(c->edges + g->edge_off, he, edge_bytes, cudaMemcpyHostToDevice, c->stream);
+    // The upload goes on the side stream: the new graph's slot and node and
+    // edge ranges are in no running launch's use (a destroyed graph's ranges
+    // are freed only after its last launch ended), so a graph can be
+    // ingested while another one runs on the context stream.  The call
+    // returns once the upload is complete.
+    cudaError_t e1 = cudaMemcpyAsync(c->edges + g->edge_off, he, edge_bytes, cudaMemcpyHostToDevice, c->side);
     cudaError_t e2 = cudaMemcpyAsync(c->slots + g->node_off, c->edges + g->pristine_off, (size_t)n * sizeof(NodeSlot),
-                                     cudaMemcpyDeviceToDevice, c->stream);
-    cudaError_t e3 = cudaMemcpyAsync(c->chunk_gid + g->chunk_off, hc, chunk_bytes, cudaMemcpyHostToDevice, c->stream);
+                                     cudaMemcpyDeviceToDevice, c->side);
+    cudaError_t e3 = cudaMemcpyAsync(c->chunk_gid + g->chunk_off, hc, chunk_bytes, cudaMemcpyHostToDevice, c->side);
     cudaError_t e4 = cudaMemcpyAsync(c->descs + g->gid, stage + edge_bytes + chunk_bytes, sizeof(GDesc),
-                                     cudaMemcpyHostToDevice, c->stream);
-    cudaError_t e5 = cudaStreamSynchronize(c->stream);
+                                     cudaMemcpyHostToDevice, c->side);
+    cudaError_t e5 = cudaStreamSynchronize(c->side);
     if (e1 || e2 || e3 || e4 || e5) {
         tg_graph_destroy(c, g);
         return TG_ERR_CUDA;

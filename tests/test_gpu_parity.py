@@ -294,3 +294,20 @@ def test_looping_graphs_never_report_a_false_race():
                 for g, h, ref in zip(graphs, hs, refs):
                     st = ex.run(h)
                     assert_same((st,) + tuple(ex.result(h)), ref, f"{g.name} {geo}")
+
+
+def test_graphs_created_while_another_runs(ex):
+    """Ingest uploads on its own stream: graphs created while a long graph
+    runs on the context stream, then run themselves, all equal the oracle."""
+    long_g = w.config2b(side=256, rounds=128)
+    others = [w.config2a(seed=31 + i, levels=30, width=300, rounds=8) for i in range(3)] + [w.config1(levels=5, width=40)]
+    h_long = ex.graph(long_g)
+    t_long = ex.submit(h_long)
+    hs = [ex.graph(g) for g in others]          # created while the long graph runs
+    assert ex.wait(t_long) == 0
+    assert_same((0,) + tuple(ex.result(h_long)), oracle.run(long_g), "long graph")
+    for g, h in zip(others, hs):
+        st = ex.run(h)
+        assert_same((st,) + tuple(ex.result(h)), oracle.run(g), g.name)
+        h.destroy()
+    h_long.destroy()
