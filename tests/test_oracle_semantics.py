@@ -146,3 +146,28 @@ def test_brute_force_init_f2_race(orc):
     assert ("RACE",) in outs
     g0 = w.nested_loops(3)
     assert len(pins.brute_force(g0, exec_cap=200, max_states=200000)) == 1
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_general_dag_matches_definition(orc, seed):
+    """Random DAGs beyond the layered shape: edges between any earlier and
+    later task (a random permutation hides the order), duplicate edges,
+    isolated tasks, wide fan-in and fan-out, mixed rounds per task."""
+    rng = random.Random(seed)
+    n = rng.randint(2, 300)
+    perm = list(range(n))
+    rng.shuffle(perm)
+    edges = []
+    for _ in range(rng.randint(0, 4 * n)):
+        a, b = sorted(rng.sample(range(n), 2))
+        edges.append((perm[a], perm[b]))
+        if rng.random() < 0.05:
+            edges.append((perm[a], perm[b]))       # a duplicate counts per edge
+    hub = perm[0]
+    edges += [(hub, perm[k]) for k in range(1, n) if rng.random() < 0.2]   # wide fan-out
+    kinds = [w.STATIC] * n
+    params = [w.pack_param(rng.randint(0, 40)) for _ in range(n)]
+    g = w.from_lists(f"random_dag_{seed}", kinds, params, edges, seed=rng.getrandbits(32))
+    r = orc.run(g)
+    assert r.status == orc.OK and r.execs == g.n
+    _same(r, pins.definitional_dag(g))
