@@ -27,7 +27,8 @@ Measured in the same run and reported beside it:
             resident scheduler (p50 / p99 latency, tasks/s) versus serving the
             same stream one launch per request
   e2e       the headline workload through the C-ABI with host buffers:
-            ingest + validate + pack + upload, run, download every result
+            ingest + validate + pack + upload, submit, wait, download every
+            result; each graph is ingested while the previous one runs
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
                   [--small] [--skip-batched] [--skip-serving] [--skip-extras]
