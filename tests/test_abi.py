@@ -48,3 +48,33 @@ def test_ctx_create_rejects_bad_arguments_without_touching_a_gpu():
     assert L.tg_ctx_create(None, 1 << 20, None, None, ctypes.byref(out)) == binding.TG_ERR_INVALID
     assert L.tg_ctx_create(ctypes.c_void_p(0x1001), 1 << 20, None, None, ctypes.byref(out)) == binding.TG_ERR_INVALID
     assert L.tg_graph_create(None, 0, None, None, 0, None, None, None, 0, ctypes.byref(out)) == binding.TG_ERR_INVALID
+
+
+def test_null_arguments_are_refused_without_touching_the_device():
+    """Every entry point that takes a context, graph or batch handle refuses
+    a null one with TG_ERR_INVALID before any CUDA call (runs without a GPU)."""
+    import ctypes
+    from paper_2004_10908_b300 import binding as B
+    L = B.load()
+    u64 = ctypes.c_uint64(0)
+    out = ctypes.c_void_p()
+    INV = B.TG_ERR_INVALID
+    assert L.tg_ctx_create(None, 1 << 20, None, None, ctypes.byref(out)) == INV
+    assert L.tg_ctx_create(ctypes.c_void_p(0x1001), 1 << 20, None, None, ctypes.byref(out)) == INV   # unaligned arena
+    assert L.tg_ctx_destroy(None) == INV
+    assert L.tg_graph_destroy(None, None) == INV
+    assert L.tg_run(None, None) == INV
+    assert L.tg_submit(None, None, ctypes.byref(u64)) == INV
+    assert L.tg_poll(None, 1) == INV
+    assert L.tg_wait(None, 1) == INV
+    assert L.tg_cancel(None) == INV
+    assert L.tg_result_copy(None, None, None, None, None, None) == INV
+    assert L.tg_batch_launch(None, None) == INV
+    assert L.tg_batch_destroy(None, None) == INV
+    assert L.tg_instance_create(None, None, ctypes.byref(out)) == INV
+    assert L.tg_serve_start(None, 0) == INV
+    assert L.tg_serve_stop(None) == INV
+    assert L.tg_graph_get_info(None, None) == INV
+    assert L.tg_ctx_get_stats(None, None) == INV
+    assert L.tg_ctx_get_opts(None, None) == INV
+    assert L.tg_ctx_set_launch(None, None) == INV
