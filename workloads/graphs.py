@@ -338,11 +338,14 @@ def config3(seed=3, n_cond=10_000, body_levels=10, body_width=10, d_lo=1, d_hi=4
                  {"lanes": meta_lanes, "S": 0, "n_cond": n_cond, "body": (body_levels, body_width)})
 
 
-def motif_graph(st: Stream, n: int, seed: int, rounds=None, r_lo=8, r_hi=512, d_lo=1, d_hi=8,
-                cond_frac=0.05, trip_max=16, name="motif") -> Graph:
+def motif_graph_py(st: Stream, n: int, seed: int, rounds=None, r_lo=8, r_hi=512, d_lo=1, d_hi=8,
+                   cond_frac=0.05, trip_max=16, name="motif") -> Graph:
     """Layered random DAG of width round(sqrt(n_d)) plus loop motifs: about
     cond_frac * n loop conditions c, each anchored on a distinct DAG task s:
-    s -> h -> c, c -> [h, arm_1 .. arm_{k-1}], k ~ U{2..4}, arms static leaves."""
+    s -> h -> c, c -> [h, arm_1 .. arm_{k-1}], k ~ U{2..4}, arms static leaves.
+
+    This is the readable definition; motif_graph() draws the same graph with
+    the native twin in motif.c (a test checks that they agree)."""
     n_c = max(1, int(round(cond_frac * n)))
     ks = st.integers(n_c, 2, 4)
     n_d = n - int((ks + 1).sum())
@@ -385,6 +388,71 @@ def motif_graph(st: Stream, n: int, seed: int, rounds=None, r_lo=8, r_hi=512, d_
     dst = np.concatenate([ed, c, cd[ok]])
     return Graph(name, kinds, params, src.astype(np.uint32), dst.astype(np.uint32), seed,
                  {"n_d": n_d, "anchors": anchors, "h": h, "c": c, "k": ks, "trips": trips})
+
+
+_motif_lib = None
+
+
+def _motif():
+    """libmotif.so, compiled from motif.c on first use (plain C, gcc)."""
+    global _motif_lib
+    if _motif_lib is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src, lib = os.path.join(here, "motif.c"), os.path.join(here, "libmotif.so")
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp, src, "-lm"])
+            os.replace(tmp, lib)
+        L = ctypes.CDLL(lib)
+        vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        L.wl_motif_graph.restype = ctypes.c_int
+        L.wl_motif_graph.argtypes = [u64, u64, u32, u32, ctypes.c_int32, u32, u32, u32, u32, u32,
+                                     vp, vp, vp, vp, u64, ctypes.POINTER(u64), vp, vp, vp,
+                                     ctypes.POINTER(u32), ctypes.POINTER(u64)]
+        _motif_lib = L
+    return _motif_lib
+
+
+def motif_graph(st: Stream, n: int, seed: int, rounds=None, r_lo=8, r_hi=512, d_lo=1, d_hi=8,
+                cond_frac=0.05, trip_max=16, name="motif") -> Graph:
+    """The motif graph of motif_graph_py, drawn by the native twin (about 50x
+    faster; the ctypes call releases the GIL, so threads generate in
+    parallel).  Advances `st` exactly as motif_graph_py does."""
+    import ctypes
+    n_c = max(1, int(round(cond_frac * n)))
+    if d_hi > 8:
+        return motif_graph_py(st, n, seed, rounds, r_lo, r_hi, d_lo, d_hi, cond_frac, trip_max, name)
+    cap = n * d_hi + 4 * n_c + 8
+    kinds = np.zeros(n, np.uint8)
+    params = np.zeros(n, np.uint32)
+    src = np.empty(cap, np.uint32)
+    dst = np.empty(cap, np.uint32)
+    ks = np.zeros(n_c, np.uint32)
+    anchors = np.zeros(n_c, np.uint32)
+    trips = np.zeros(n_c, np.uint32)
+    m = ctypes.c_uint64(0)
+    n_d = ctypes.c_uint32(0)
+    pos = ctypes.c_uint64(0)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = _motif().wl_motif_graph(st.state, st.pos, n, n_c, -1 if rounds is None else int(rounds), r_lo, r_hi,
+                                 d_lo, d_hi, trip_max, ptr(kinds), ptr(params), ptr(src), ptr(dst), cap,
+                                 ctypes.byref(m), ptr(ks), ptr(anchors), ptr(trips), ctypes.byref(n_d),
+                                 ctypes.byref(pos))
+    if rc == -1:
+        raise ValueError("graph too small for its motifs")
+    if rc != 0:
+        raise RuntimeError(f"wl_motif_graph failed ({rc})")
+    st.pos = pos.value
+    nd = int(n_d.value)
+    sizes = ks.astype(np.int64) + 1
+    base = nd + np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    mm = int(m.value)
+    return Graph(name, kinds, params, src[:mm].copy(), dst[:mm].copy(), seed,
+                 {"n_d": nd, "anchors": anchors.astype(np.int64), "h": base, "c": base + 1,
+                  "k": ks.astype(np.int64), "trips": trips.astype(np.int64)})
 
 
 def _logu(st: Stream, lo: int, hi: int) -> int:
