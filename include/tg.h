@@ -196,18 +196,25 @@ typedef struct {
 int tg_graph_get_info(const tg_graph *g, tg_graph_info *info);
 
 /* Run one graph: re-arm its state, launch the persistent scheduler on the
- * context stream and wait.  Returns the graph's final status (TG_OK, or
+ * context stream and wait -- the paper's "executor.run(taskflow).wait()"
+ * (Static Tasking).  Returns the graph's final status (TG_OK, or
  * TG_ERR_RACE / EXEC_LIMIT / TIMEOUT / CANCELLED / INTERNAL / CUDA). */
 int tg_run(tg_ctx *ctx, tg_graph *g);
 
-/* Asynchronous form: enqueue the run and return at once.  *ticket names the
- * submission for tg_poll / tg_wait; it stays valid until g is submitted
- * again or destroyed (a new submission of g releases g's earlier tickets).
- * TG_ERR_BUSY if g is still in flight. */
+/* Asynchronous form: enqueue the run and return at once -- submit_graph of
+ * Algorithm 8 (the tasks with zero strong and zero weak dependencies go to
+ * the shared queue first; here the re-arm kernel places them in the
+ * injection queue the scheduler's thieves read).  *ticket names the
+ * submission for tg_poll / tg_wait (the paper's run() returns a future);
+ * it stays valid until g is submitted again or destroyed (a new submission
+ * of g releases g's earlier tickets).  TG_ERR_BUSY if g is still in flight
+ * (a graph must not run twice at once, Composable Tasking). */
 int tg_submit(tg_ctx *ctx, tg_graph *g, uint64_t *ticket);
-/* Never blocks: TG_PENDING while the run is in flight, else its status. */
+/* Never blocks: TG_PENDING while the run is in flight, else its status (a
+ * non-blocking look at the future's state). */
 int tg_poll(tg_ctx *ctx, uint64_t ticket);
-/* Blocks until the submission finished; returns its status. */
+/* Blocks until the submission finished; returns its status (the future's
+ * wait(), Static Tasking). */
 int tg_wait(tg_ctx *ctx, uint64_t ticket);
 
 /* Make another execution instance of graph g: its own task state, outputs
@@ -236,19 +243,24 @@ int tg_serve_start(tg_ctx *ctx, uint64_t time_limit_ns);
  * that ended it (TG_ERR_TIMEOUT, TG_ERR_INTERNAL). */
 int tg_serve_stop(tg_ctx *ctx);
 
-/* Request loop over a running server: request i arrives arrival_ns[i] after
- * the call starts (ascending) and asks for one execution of
- * templates[which[i]].  It is admitted as soon as an instance fits the
- * memory budget and a graph slot is free (FIFO otherwise), submitted while
- * other requests run, and its instance is destroyed the moment it finishes,
- * freeing budget for waiting requests.  Per request: latency_ns[i] = finish
- * minus arrival on the host clock, status[i].  *max_in_flight (nullable)
- * receives the most requests on the device at once.  keep (nullable, n
- * entries) receives each finished instance instead of destroying it (the
- * caller destroys them).  Returns TG_OK or the first request's error. */
+/* Request loop over a running server (the paper's co-run experiments run
+ * many task graphs at once on one executor; here they are admitted while
+ * others run): request i arrives arrival_ns[i] after the call starts
+ * (ascending) and asks for one execution of templates[which[i]].  It is
+ * admitted as soon as an instance fits the memory budget and a graph slot is
+ * free (FIFO otherwise), submitted while other requests run, and its
+ * instance is destroyed the moment it finishes, freeing budget for waiting
+ * requests.  Per request: latency_ns[i] = finish minus arrival on the host
+ * clock, status[i].  *max_in_flight (nullable) receives the most requests on
+ * the device at once.  keep (nullable, n entries) receives each finished
+ * instance instead of destroying it -- every request's, or with keep_mask
+ * (nullable) only those whose mask byte is non-zero, the others getting
+ * NULL -- so that its per-task results can be read with tg_result_copy; the
+ * caller destroys kept instances, whose memory counts against the budget
+ * until then.  Returns TG_OK or the first request's error. */
 int tg_serve_replay(tg_ctx *ctx, tg_graph *const *templates, uint32_t n_templates, const uint32_t *which,
                     const uint64_t *arrival_ns, uint32_t n_requests, uint64_t *latency_ns, int *status,
-                    uint32_t *max_in_flight, tg_graph **keep);
+                    uint32_t *max_in_flight, tg_graph **keep, const uint8_t *keep_mask);
 
 /* Ask the device to stop: running graphs end with TG_ERR_CANCELLED (the
  * workers poll a host-mapped flag; the flag is cleared at the next launch). */
@@ -256,7 +268,14 @@ int tg_cancel(tg_ctx *ctx);
 
 /* Copy the per-task results of g's last run to host arrays of n entries
  * (any pointer may be NULL); total_execs = sum of cnt.  Synchronises the
- * context stream. */
+ * context stream.  (The paper's tasks keep their results in user data; here
+ * every task's last output, execution count and digest stay in the graph's
+ * device state until its next run.)  Results are read by graph, not by
+ * ticket: a graph holds the state of its last run, while a ticket only
+ * names a submission.  A served request runs on an instance that the request
+ * loop destroys when it finishes, freeing its memory for waiting requests;
+ * to read a served request's results, keep its instance (tg_serve_replay's
+ * keep / keep_mask) and pass that instance here. */
 int tg_result_copy(tg_ctx *ctx, const tg_graph *g, uint32_t *out, uint32_t *cnt, uint32_t *dig,
                    uint64_t *total_execs);
 
@@ -295,7 +314,9 @@ int tg_graph_autotune(tg_ctx *ctx, tg_graph *g, uint32_t trials, const char *cac
                       uint64_t *best_ns);
 
 /* Convenience: create, launch, wait and destroy; statuses may be NULL.
- * Returns TG_OK if every graph ended TG_OK, else the first error. */
+ * Returns TG_OK if every graph ended TG_OK, else the first error.  (The
+ * paper runs several task graphs on one executor at once, co-run
+ * experiments of Micro-benchmarks; here they share one persistent launch.) */
 int tg_run_batch(tg_ctx *ctx, tg_graph *const *gs, uint32_t n, int *statuses);
 
 /* Scheduler counters of the context's last launch (summed over blocks). */
@@ -384,11 +405,16 @@ int tg_capture_run(tg_ctx *ctx, tg_graph *g, uint32_t max_streams, uint64_t *ns)
  *   out[n], cnt[n], dig[n]    device outputs (any may be NULL)
  *   cuda_stream               stream the work is enqueued on; the call
  *                             synchronises it before returning
- * Limits: n <= 65536 tasks and m <= 262144 edges, else TG_ERR_BUDGET.
- * Returns the validation status (as tg_graph_create) or the run's status.
+ * Limits: n <= 65536 tasks and m <= 262144 edges, else TG_ERR_BUDGET; the
+ * scratch array is 6,892,032 bytes (about 6.6 MiB).
+ * Returns the validation status (as tg_graph_create, checked on the device:
+ * TG_ERR_INVALID also for a successor id >= n, succ_off decreasing or past
+ * n_edges, or succ_off[n] != n_edges) or the run's status.
  * Every call shares the one scratch array: calls that overlap on the GPU
  * race.  The first call on a device sets that device up (looks up the
- * array's address), so make it before any stream capture. */
+ * array's address).  The call cannot be made while cuda_stream is being
+ * captured into a CUDA graph: it synchronises the stream and reads status
+ * words back to the host. */
 int tg_run_noalloc(uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
                    const uint32_t *succ_off, const uint32_t *succ, uint32_t n_edges, uint32_t seed,
                    uint32_t *out, uint32_t *cnt, uint32_t *dig, void *cuda_stream);

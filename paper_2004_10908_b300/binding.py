@@ -99,7 +99,7 @@ SIGNATURES = {
     "tg_instance_create": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
     "tg_serve_start": (ctypes.c_int, [_vp, _u64]),
     "tg_serve_stop": (ctypes.c_int, [_vp]),
-    "tg_serve_replay": (ctypes.c_int, [_vp, _vp, _u32, _vp, _vp, _u32, _vp, _vp, ctypes.POINTER(_u32), _vp]),
+    "tg_serve_replay": (ctypes.c_int, [_vp, _vp, _u32, _vp, _vp, _u32, _vp, _vp, ctypes.POINTER(_u32), _vp, _vp]),
     "tg_batch_autotune": (ctypes.c_int, [_vp, _vp, _u32, ctypes.c_char_p, ctypes.POINTER(tg_ctx_opts),
                                          ctypes.POINTER(_u64)]),
     "tg_bench_payload": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
@@ -289,19 +289,27 @@ def tg_serve_stop(ctx) -> int:
 
 
 def tg_serve_replay(ctx, templates, which, arrival_ns, keep=False):
-    """Returns (status, latency_ns[], status[], max_in_flight, kept instance handles or None)."""
+    """Returns (status, latency_ns[], status[], max_in_flight, kept instance
+    handles or None).  keep: False, True (every request) or a boolean mask of
+    the requests whose instances are kept."""
     which = np.ascontiguousarray(which, dtype=np.uint32)
     arrival = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
     n = which.shape[0]
     lat = np.zeros(n, np.uint64)
     sts = np.zeros(n, np.int32)
     peak = _u32(0)
-    kept = (_vp * n)() if keep else None
+    want = keep is not False and keep is not None
+    kept = (_vp * n)() if want else None
+    mask = None
+    if want and keep is not True:
+        mask = np.ascontiguousarray(np.asarray(keep, dtype=bool).astype(np.uint8))
+        assert mask.shape[0] == n
     st = load().tg_serve_replay(_vp(ctx), ctypes.cast(_handles(templates), _vp), len(templates),
                                 which.ctypes.data_as(_vp), arrival.ctypes.data_as(_vp), n,
                                 lat.ctypes.data_as(_vp), sts.ctypes.data_as(_vp), ctypes.byref(peak),
-                                ctypes.cast(kept, _vp) if keep else None)
-    return st, lat, sts, peak.value, ([kept[i] for i in range(n)] if keep else None)
+                                ctypes.cast(kept, _vp) if want else None,
+                                mask.ctypes.data_as(_vp) if mask is not None else None)
+    return st, lat, sts, peak.value, ([kept[i] for i in range(n)] if want else None)
 
 
 def tg_ctx_set_launch(ctx, **fields) -> int:

@@ -106,11 +106,12 @@ struct RangeAlloc {
 }  // namespace
 
 // A graph owns its packed form in the edge pool -- successor lists (graph-
-// local ids), the source list and a pristine image of its 32-byte task
-// records -- and an execution instance: a chunk-aligned range of the node
-// pool (task records + join/execution state + outputs) and a descriptor
-// slot (gid).  An instance made by tg_instance_create shares its template's
-// packed form and owns only an execution range and a gid.
+// local ids) and the source list -- and an execution instance: a chunk-
+// aligned range of the node pool (task records + join/execution state +
+// outputs) and a descriptor slot (gid).  An instance made by
+// tg_instance_create shares its template's packed form and owns only an
+// execution range and a gid; its records are re-armed from the immutable
+// half of the template's own records.
 struct tg_graph {
     tg_ctx *ctx = nullptr;
     tg_graph *tmpl = nullptr;     // the graph whose packed form this instance uses
@@ -118,7 +119,7 @@ struct tg_graph {
     u32 gid = 0;
     u32 n = 0, m = 0, n_src = 0, n_cond = 0;
     u64 node_off = 0, chunk_off = 0, n_chunks = 0;
-    u64 edge_off = 0, edge_len = 0, pristine_off = 0;
+    u64 edge_off = 0, edge_len = 0;
     u32 seed = 0;
     u64 pack_ns = 0, upload_ns = 0, bytes = 0;
     cudaEvent_t busy = nullptr;   // event of the launch it is in (null: idle)
@@ -446,8 +447,8 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
     u64 ncap = o.max_nodes, ecap = o.max_edges;
     ncap &= ~(u64)(kChunk - 1);
     if (ncap == 0) {
-        // per task: 36 B execution range + 8 B of injection queue + 32 B
-        // pristine image + successors (about 8 x 4 B) in the edge pool
+        // per task: 36 B execution range + 8 B of injection queue; the edge
+        // pool (successor lists and sources) takes the rest
         ncap = (rest / ((o.flags & TG_OPT_TRACE) ? 144 : 128)) & ~(u64)255;
         if (ncap > kMaxNodeIndex)
             ncap = kMaxNodeIndex & ~(u64)255;
@@ -652,9 +653,9 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
         return TG_ERR_NO_SOURCE;
 
     // ---- pool space: a chunk-aligned execution range, and in the edge pool
-    // the successor lists, the sources and the pristine record image
+    // the successor lists and the sources
     const u64 n_chunks = ((u64)n + kChunk - 1) >> kChunkShift;
-    const u64 bytes = n_chunks * kChunk * 36 + ((u64)m + n_mod + n_src + 64 + 8ull * n) * 4;
+    const u64 bytes = n_chunks * kChunk * 36 + ((u64)m + n_mod + n_src) * 4;
     if (c->used + bytes > c->budget || c->free_gids.empty())
         return TG_ERR_BUDGET;
     tg_graph *g = new (std::nothrow) tg_graph();
@@ -667,18 +668,15 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
     c->live_graphs.insert(g);
     g->n_chunks = n_chunks;
     g->node_off = g->chunk_off << kChunkShift;
-    // the pristine image starts on a 256-byte boundary (64 entries), so its
-    // device-to-device copies stay on the copy engines
     // a module task's list is led by the slot id of the graph it composes
     const u64 lead = (u64)m + n_mod + n_src;
-    g->edge_len = lead + 64 + 8ull * n;
+    g->edge_len = lead;
     if (!c->edge_pool.alloc(g->edge_len, g->edge_off)) {
         c->nodes.release(g->chunk_off, n_chunks);
         c->live_graphs.erase(g);
         delete g;
         return TG_ERR_BUDGET;
     }
-    g->pristine_off = (g->edge_off + lead + 63) & ~(u64)63;
     g->gid = c->free_gids.back();
     c->free_gids.pop_back();
     c->used += bytes;
@@ -695,7 +693,10 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
     // then the 32-byte task records (W = strong in-degree, cnt = dig = 0)
     const size_t edge_bytes = (size_t)g->edge_len * 4;
     const size_t chunk_bytes = (size_t)n_chunks * 4;
-    int rc = ensure_stage(c, edge_bytes + chunk_bytes + 512);
+    // staging: successor lists, chunk table, descriptor, then the records on
+    // a 256-byte boundary
+    const size_t rec_at = ((g->edge_off & 63u) * 4u + edge_bytes + chunk_bytes + sizeof(GDesc) + 255) & ~(size_t)255;
+    int rc = ensure_stage(c, rec_at + (size_t)n * sizeof(NodeSlot));
     if (rc != TG_OK) {
         tg_graph_destroy(c, g);
         return rc;
@@ -712,11 +713,11 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
                 g->sub_insts.push_back(inst);
             }
     cudaStreamSynchronize(c->side);   // the staging buffer may still feed an earlier upload
-    // the staging image starts at the same offset within 256 bytes as its
-    // device copy, so the records start on a 256-byte boundary here too
+    // the staged successor lists start at the same offset within 256 bytes
+    // as their device copy
     char *stage = c->h_stage + (g->edge_off & 63u) * 4u;
     u32 *he = (u32 *)stage;
-    NodeSlot *hs = (NodeSlot *)(he + (g->pristine_off - g->edge_off));
+    NodeSlot *hs = (NodeSlot *)(c->h_stage + rec_at);
     u32 *hc = (u32 *)(stage + edge_bytes);
     const bool stream_records = ((uintptr_t)hs & 15u) == 0u;
     const u32 edge_base = (u32)g->edge_off;
@@ -794,8 +795,8 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
     // ingested while another one runs on the context stream.  The call
     // returns once the upload is complete.
     cudaError_t e1 = cudaMemcpyAsync(c->edges + g->edge_off, he, edge_bytes, cudaMemcpyHostToDevice, c->side);
-    cudaError_t e2 = cudaMemcpyAsync(c->slots + g->node_off, c->edges + g->pristine_off, (size_t)n * sizeof(NodeSlot),
-                                     cudaMemcpyDeviceToDevice, c->side);
+    cudaError_t e2 = cudaMemcpyAsync(c->slots + g->node_off, hs, (size_t)n * sizeof(NodeSlot),
+                                     cudaMemcpyHostToDevice, c->side);
     cudaError_t e3 = cudaMemcpyAsync(c->chunk_gid + g->chunk_off, hc, chunk_bytes, cudaMemcpyHostToDevice, c->side);
     cudaError_t e4 = cudaMemcpyAsync(c->descs + g->gid, stage + edge_bytes + chunk_bytes, sizeof(GDesc),
                                      cudaMemcpyHostToDevice, c->side);
@@ -827,8 +828,8 @@ int tg_graph_create_composed(tg_ctx *c, uint32_t n, const uint8_t *kinds, const 
 
 }  // extern "C"
 
-// Write an instance's records (from the pristine image), chunk table and
-// descriptor on the side stream; later launches wait for `ready`.
+// Write an instance's records (re-armed from the template's records), chunk
+// table and descriptor on the side stream; later launches wait for `ready`.
 static int instance_setup(tg_ctx *c, tg_graph *g)
 {
     tg_graph *src = g->tmpl ? g->tmpl : g;
@@ -840,8 +841,7 @@ static int instance_setup(tg_ctx *c, tg_graph *g)
     d.src_off = (u32)(src->edge_off + src->m);
     d.n_src = g->n_src;
     d.exec_cap = (u32)std::min<u64>(c->opts.exec_cap, 0xFFFFFFFFull);
-    TG_CUDA(cudaMemcpyAsync(c->slots + g->node_off, c->edges + src->pristine_off, (size_t)g->n * sizeof(NodeSlot),
-                            cudaMemcpyDeviceToDevice, c->side));
+    TG_CUDA(launch_instance_rearm(c->slots, src->node_off, g->node_off, g->n, c->side));
     TG_CUDA(cudaMemcpyAsync(c->chunk_gid + g->chunk_off, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice, c->side));
     TG_CUDA(cudaMemcpyAsync(c->descs + g->gid, &d, sizeof(d), cudaMemcpyHostToDevice, c->side));
     if (!g->ready)
@@ -1318,11 +1318,13 @@ int tg_graph_dot(tg_ctx *c, const tg_graph *g, char *buf, size_t cap, size_t *le
     if (!c || !g || g->ctx != c || !len)
         return TG_ERR_INVALID;
     const tg_graph *t = g->tmpl ? g->tmpl : g;
+    // (the immutable half of the template's own records: successor range,
+    // degrees, kind and parameters)
     std::vector<NodeSlot> rec(g->n);
-    std::vector<u32> ed(t->pristine_off - t->edge_off);
+    std::vector<u32> ed(t->edge_len);
     if (!c->serving)
         TG_CUDA(cudaStreamSynchronize(c->stream));
-    TG_CUDA(cudaMemcpy(rec.data(), c->edges + t->pristine_off, (size_t)g->n * sizeof(NodeSlot),
+    TG_CUDA(cudaMemcpy(rec.data(), c->slots + t->node_off, (size_t)g->n * sizeof(NodeSlot),
                        cudaMemcpyDeviceToHost));
     if (!ed.empty())
         TG_CUDA(cudaMemcpy(ed.data(), c->edges + t->edge_off, ed.size() * 4, cudaMemcpyDeviceToHost));
@@ -1388,7 +1390,7 @@ int tg_capture_run(tg_ctx *c, tg_graph *g, uint32_t max_streams, uint64_t *ns)
         std::vector<NodeSlot> rec(g->n);
         std::vector<u32> ed(t->m);
         TG_CUDA(cudaStreamSynchronize(c->stream));
-        TG_CUDA(cudaMemcpy(rec.data(), c->edges + t->pristine_off, (size_t)g->n * sizeof(NodeSlot),
+        TG_CUDA(cudaMemcpy(rec.data(), c->slots + t->node_off, (size_t)g->n * sizeof(NodeSlot),
                            cudaMemcpyDeviceToHost));
         if (t->m)
             TG_CUDA(cudaMemcpy(ed.data(), c->edges + t->edge_off, (size_t)t->m * 4, cudaMemcpyDeviceToHost));
@@ -2088,9 +2090,9 @@ static int serve_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     if (g->serve_ticket != 0 || graph_busy(g))
         return TG_ERR_BUSY;
     tg_graph *src = g->tmpl ? g->tmpl : g;
-    // re-arm on the side stream: fresh task records from the pristine image
-    // (join words, counts, digests), then the ring entry -- stream order makes
-    // the records visible before the scheduler can see the entry
+    // re-arm on the side stream: fresh task records from the template's
+    // (join words, counts, digests), then the ring entry -- stream order
+    // makes the records visible before the scheduler can see the entry
     const u64 seq = c->sub_seq++;
     SubEntry &h = c->h_sub[seq & (kSubRing - 1u)];
     h.seq = (u32)(seq + 1u);
@@ -2102,8 +2104,7 @@ static int serve_submit(tg_ctx *c, tg_graph *g, uint64_t *ticket)
     h.n_src = g->n_src;
     h.exec_cap = (u32)std::min<u64>(c->opts.exec_cap, 0xFFFFFFFFull);
     g->setup_pending = false;   // the scheduler writes descriptor and chunk table on claim
-    TG_CUDA(cudaMemcpyAsync(c->slots + g->node_off, c->edges + src->pristine_off, (size_t)g->n * sizeof(NodeSlot),
-                            cudaMemcpyDeviceToDevice, c->side));
+    TG_CUDA(launch_instance_rearm(c->slots, src->node_off, g->node_off, g->n, c->side));
     // the entry's fields first, its sequence word last: a scheduler that sees
     // the new seq then reads complete fields (stream order of the copies)
     SubEntry *dst = &c->sub[seq & (kSubRing - 1u)];
@@ -2221,13 +2222,18 @@ int tg_serve_stop(tg_ctx *c)
 
 extern "C" int tg_serve_replay(tg_ctx *c, tg_graph *const *templates, uint32_t n_templates, const uint32_t *which,
                                const uint64_t *arrival_ns, uint32_t n_requests, uint64_t *latency_ns, int *status,
-                               uint32_t *max_in_flight, tg_graph **keep)
+                               uint32_t *max_in_flight, tg_graph **keep, const uint8_t *keep_mask)
 {
     if (!c || !c->serving || !templates || !which || !arrival_ns || !latency_ns || !status)
         return TG_ERR_INVALID;
     for (uint32_t i = 0; i < n_requests; ++i)
         if (which[i] >= n_templates || !templates[which[i]] || templates[which[i]]->ctx != c)
             return TG_ERR_INVALID;
+    if (keep)
+        for (uint32_t i = 0; i < n_requests; ++i)
+            keep[i] = nullptr;
+    // request r's instance is kept (not destroyed) when it finishes
+    auto kept = [&](uint32_t r) { return keep && (!keep_mask || keep_mask[r]); };
     struct Flight {
         uint32_t req;
         tg_graph *inst;
@@ -2284,7 +2290,7 @@ extern "C" int tg_serve_replay(tg_ctx *c, tg_graph *const *templates, uint32_t n
                 latency_ns[r] = now > arrival_ns[r] ? now - arrival_ns[r] : 0;
                 if (st != TG_OK && first_err == TG_OK)
                     first_err = st;
-                if (keep)
+                if (kept(r))
                     keep[r] = it->second.inst;
                 else
                     tg_graph_destroy(c, it->second.inst);
@@ -2298,7 +2304,7 @@ extern "C" int tg_serve_replay(tg_ctx *c, tg_graph *const *templates, uint32_t n
             // the resident scheduler ended (time limit / fault): fail the rest
             for (auto &kv : flight) {
                 status[kv.second.req] = TG_ERR_TIMEOUT;
-                if (keep)
+                if (keep)   // still named by the server's records: the caller destroys it after stopping
                     keep[kv.second.req] = kv.second.inst;
                 done++;
             }

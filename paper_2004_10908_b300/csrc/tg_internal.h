@@ -172,6 +172,10 @@ size_t sched_dyn_smem(u32 smem_entries, u32 warps);
 cudaError_t launch_bench_payload(u64 count, u32 rounds, u32 *checksum, cudaStream_t st);
 cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink, cudaStream_t st);
 cudaError_t launch_bench_chain(u32 hops, u32 rounds, u32 *last, cudaStream_t st);
+// Fresh records for an instance: the immutable half of the template's records
+// at src_off (successor range, degrees, kind, parameters, id), join word =
+// strong in-degree, count = digest = 0, written at dst_off (may equal src_off).
+cudaError_t launch_instance_rearm(NodeSlot *slots, u64 src_off, u64 dst_off, u32 n, cudaStream_t st);
 cudaError_t launch_capture_task(NodeSlot *slots, u32 *outv, const u32 *edges, u32 u, u32 node_off, cudaStream_t st);
 // tg_result.cu: pack the count and digest of tasks [node_off, node_off + n) into dst[0, n)
 cudaError_t launch_result_gather(const NodeSlot *slots, u32 node_off, u32 n, u64 *dst, cudaStream_t st);

@@ -278,6 +278,7 @@ struct WarpCtx {
     u32 high_water;  // local ring size above which new work goes public while a block is hungry
     u32 keep_hi;     // local ring size above which new work always goes public
     const u32 *hungry;  // blocks whose thief found no work anywhere
+    u32 hungry_v;       // lane 0: its value, loaded at the start of the warp's step
     u32 *avail_word; // this block's word / bit in the work-available bitmap
     u32 avail_bit;
     int err;
@@ -289,11 +290,12 @@ __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u3
     if (__ballot_sync(kFull, has) == 0)
         return;
     // spill beyond a short backlog while some block is idle, beyond a long
-    // one otherwise (the hungry count is read only past the short mark)
+    // one otherwise (the hungry count was loaded when the step began, so
+    // its latency is not on the publication path)
     int spill = 0;
     if (lane == 0) {
         const u32 lsz = ring_size<true>(w.local);
-        spill = lsz >= w.keep_hi || (lsz >= w.high_water && (i32)vld32(w.hungry) > 0);
+        spill = lsz >= w.keep_hi || (lsz >= w.high_water && (i32)w.hungry_v > 0);
     }
     spill = __shfl_sync(kFull, spill, 0);
     bool pub = has && spill;
@@ -479,6 +481,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     w.high_water = min(p.local_keep ? p.local_keep : 32u, ring_n);
     w.keep_hi = max(w.high_water, ring_n / 2u);
     w.hungry = &p.ctl->hungry;
+    w.hungry_v = 0;
     w.err = 0;
     w.avail_word = &p.ctl->avail[blockIdx.x >> 5];
     w.avail_bit = 1u << (blockIdx.x & 31u);
@@ -717,7 +720,13 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                     st_fail++;
                     int stop = 0;
                     if (lane == 0) {
-                        const bool done = kServe ? (vld32(&p.ctl->stop) != 0u) : (vld32(&p.ctl->graphs_left) == 0u);
+                        bool done = kServe ? (vld32(&p.ctl->stop) != 0u) : (vld32(&p.ctl->graphs_left) == 0u);
+                        // kAcyc: settled by reductions, so the graph is done
+                        // when a thief finds nothing pending
+                        if (kAcyc && !done && (u32)vld64(&p.descs[p.single_gid].pe) == 0u) {
+                            done = true;
+                            atomicExch(&p.ctl->graphs_left, 0u);
+                        }
                         if (done || vldi(&p.ctl->abort_code) != 0) {
                             stop = 1;
                         } else if (globaltimer() > deadline) {
@@ -817,6 +826,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         }
         if (lane == 0 && *(volatile int *)&s_hungry != 0 && atomicExch(&s_hungry, 0) == 1)
             atomicSub(&p.ctl->hungry, 1u);
+        if (lane == 0)
+            w.hungry_v = vld32(w.hungry);   // used when the step publishes
 
         // ---- read the activations' tasks
         bool act = lane < k && (u32)e != kEmpty32;
@@ -881,6 +892,9 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             asm volatile("" ::"r"(maxc), "r"(iter), "r"(lid), "r"(c_seed));
             mark(1);
         }
+        // The loads leave raw successor words in s_; decode() turns them
+        // into node-pool ids later, so that the first round's loads stay in
+        // flight while the payload runs.
         u32 s_[kRelUnroll], ow_[kRelUnroll];
         bool v_[kRelUnroll];
         u32 total = 0, excl = 0;
@@ -889,8 +903,15 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             for (int j = 0; j < kRelUnroll; ++j) {
                 v_[j] = j0 + (u32)j < c;
                 ow_[j] = (u32)lane;
-                const u32 r = v_[j] ? ld_imm<kServe>(&p.edges[succ_off + j0 + (u32)j]) : 0u;
-                s_[j] = v_[j] ? (c_base + (r & ~kSoleBit)) | (r & kSoleBit) : 0u;
+                s_[j] = v_[j] ? ld_imm<kServe>(&p.edges[succ_off + j0 + (u32)j]) : 0u;
+            }
+        };
+        // (the base of the owner's graph: an idle lane may own no graph)
+        auto decode = [&]() {
+#pragma unroll
+            for (int j = 0; j < kRelUnroll; ++j) {
+                const u32 base_o = __shfl_sync(kFull, c_base, (int)ow_[j]);
+                s_[j] = v_[j] ? (base_o + (s_[j] & ~kSoleBit)) | (s_[j] & kSoleBit) : 0u;
             }
         };
         auto fetch_flat = [&](u32 base) {
@@ -908,10 +929,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 }
                 const u32 off_o = __shfl_sync(kFull, succ_off, o);
                 const u32 ex_o = __shfl_sync(kFull, excl, o);
-                const u32 base_o = __shfl_sync(kFull, c_base, o);
                 ow_[j] = (u32)o;
-                const u32 r = v_[j] ? ld_imm<kServe>(&p.edges[off_o + (eq - ex_o)]) : 0u;
-                s_[j] = v_[j] ? (base_o + (r & ~kSoleBit)) | (r & kSoleBit) : 0u;
+                s_[j] = v_[j] ? ld_imm<kServe>(&p.edges[off_o + (eq - ex_o)]) : 0u;
             }
         };
         if (per_lane) {
@@ -930,8 +949,17 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             fetch_flat(0u);
         }
 
-        // the previous iteration's pending-count update arrives meanwhile
-        resume(settle_finish<kServe, kExt>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
+        // A condition's choice depends on its id and count, not on its
+        // output: its successor is fetched before the payload too.
+        int c_r = -1;
+        u32 c_raw = 0;
+        if (!kAcyc && act && c_status == 0 && kind >= TG_COND_BRANCH && kind <= TG_COND_CONST) {
+            c_r = cond_index(kind, arg, c_seed, lid, iter, succ_cnt);
+            if (c_r >= 0 && (u32)c_r < succ_cnt)
+                c_raw = ld_imm<kServe>(&p.edges[succ_off + (u32)c_r]);
+            else
+                c_r = -1;
+        }
 
         // a strong activation consumed its join word: re-arm it for the next
         // round (composes with releases of that round that arrive early); a
@@ -950,6 +978,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         const bool sink_acc = modules && act && c_status == 0 && kind == TG_STATIC && succ_cnt == 0u;
         if (sink_acc)
             atomicAdd(&p.descs[gid].acc, x);
+        // the previous iteration's pending-count update has arrived meanwhile
+        resume(settle_finish<kServe, kExt>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
         if (traced) {
             asm volatile("" ::"r"(dg));
             mark(2);
@@ -1005,18 +1035,15 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         // ---- condition tasks: jump to successors[r]
         bool c_has = false;
         u32 c_t = 0, c_fl = 0;
-        if (run && kind >= TG_COND_BRANCH && kind <= TG_COND_CONST) {
-            int r = cond_index(kind, arg, c_seed, lid, iter, succ_cnt);
-            if (r >= 0 && (u32)r < succ_cnt) {
-                c_t = c_base + (ld_imm<kServe>(&p.edges[succ_off + (u32)r]) & ~kSoleBit);
-                c_has = true;
-                mp++;
-                if (race_check) {
-                    if (c_t == u)
-                        keep_self = true;
-                    else
-                        c_fl = atomicOr(&p.slots[c_t].cnt, kInflight);
-                }
+        if (run && c_r >= 0) {
+            c_t = c_base + (c_raw & ~kSoleBit);
+            c_has = true;
+            mp++;
+            if (race_check) {
+                if (c_t == u)
+                    keep_self = true;
+                else
+                    c_fl = atomicOr(&p.slots[c_t].cnt, kInflight);
             }
         }
 
@@ -1025,6 +1052,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             for (u32 j0 = 0; j0 < maxc; j0 += kRelUnroll) {
                 if (j0)
                     fetch_lane(j0);
+                decode();
                 u64 old_[kRelUnroll];
                 u32 fl_[kRelUnroll];
                 bool has_[kRelUnroll];
@@ -1076,6 +1104,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 u32 xo_[kRelUnroll], go_[kRelUnroll], fl_[kRelUnroll];
                 u64 old_[kRelUnroll], ent_[kRelUnroll];
                 bool has_[kRelUnroll];
+                decode();
 #pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j) {
                     xo_[j] = __shfl_sync(kFull, x, (int)ow_[j]);
@@ -1262,10 +1291,18 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 if (lane == 0 && E) {
                     const long long d = (long long)sumP - (long long)sumU - (long long)E;
                     pend_delta = ((u64)E << 32) + (u64)d;   // (no continuations without modules)
-                    pend_old = atomicAdd(&p.descs[p.single_gid].pe, pend_delta);
-                    pend_g = p.single_gid;
-                    pend_cap = single_cap;
-                    pend = true;
+                    if (kAcyc) {
+                        // every task runs at most once, so the cap needs no
+                        // check on the way: a reduction (its returned value
+                        // would hold the warp up), and idle thieves notice
+                        // the pending count reach zero
+                        atomicAdd(&p.descs[p.single_gid].pe, pend_delta);
+                    } else {
+                        pend_old = atomicAdd(&p.descs[p.single_gid].pe, pend_delta);
+                        pend_g = p.single_gid;
+                        pend_cap = single_cap;
+                        pend = true;
+                    }
                 }
             } else {
                 u32 rem = __ballot_sync(kFull, act);
@@ -1417,6 +1454,18 @@ __global__ void rearm_kernel(KParams p)
     }
 }
 
+// An instance's records from its template's (immutable half read through
+// L2: the template may be running, which changes only the other half).
+__global__ void instance_rearm_kernel(NodeSlot *slots, u64 src_off, u64 dst_off, u32 n)
+{
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint4 imm = __ldcg(reinterpret_cast<const uint4 *>(&slots[src_off + i]));
+        uint4 *d = reinterpret_cast<uint4 *>(&slots[dst_off + i]);
+        d[0] = imm;
+        d[1] = make_uint4(imm.y >> 16, 0u, 0u, 0u);   // W = {insum 0 | strong in-degree}, cnt, dig
+    }
+}
+
 // A graph composed by a module task of the launch: its state starts from
 // scratch, idle (nothing pending, no module task to resume), sources not
 // activated -- its module task does that.
@@ -1454,6 +1503,12 @@ __global__ void finalize_kernel(KParams p)
         if (st == 0 && (u32)D.pe != 0u) {
             i32 ab = p.ctl->abort_code;
             st = ab != 0 ? ab : TG_ERR_INTERNAL;
+            D.status = st;
+        }
+        // (the lean kernel for a graph without condition tasks counts
+        // executions without checking them against the cap as it goes)
+        if (st == 0 && (u32)(D.pe >> 32) > D.exec_cap) {
+            st = TG_ERR_EXEC_LIMIT;
             D.status = st;
         }
         if (p.status_out)
@@ -1670,6 +1725,15 @@ cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink
 cudaError_t launch_bench_chain(u32 hops, u32 rounds, u32 *last, cudaStream_t st)
 {
     bench_chain_kernel<<<1, 1, 0, st>>>(hops, rounds, last);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_instance_rearm(NodeSlot *slots, u64 src_off, u64 dst_off, u32 n, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const u32 blocks = min((n + 255u) / 256u, 2048u);
+    instance_rearm_kernel<<<blocks, 256, 0, st>>>(slots, src_off, dst_off, n);
     return cudaGetLastError();
 }
 

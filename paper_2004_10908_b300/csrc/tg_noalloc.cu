@@ -9,12 +9,14 @@
 // The array exists on every GPU that loads the library until the process
 // exits.  The caller passes device pointers to its inputs and outputs.
 //
-// Limits: at most kNaMaxNodes tasks and kNaMaxEdges edges per call.
+// Limits: at most kNaMaxNodes tasks and kNaMaxEdges edges per call; the
+// array holds kScratchBytes = 6,892,032 bytes (about 6.6 MiB).
 // Every call shares the array: calls that overlap on the GPU (from several
 // host threads or streams) race and corrupt each other.  The first call on
 // a device looks up the array's device address (cudaGetSymbolAddress) and
-// configures the kernel, so that first call should be made before any
-// stream capture.
+// configures the kernel.  No call can be made while its stream is being
+// captured into a CUDA graph: every call synchronises the stream and reads
+// status words back to the host.
 #include <cstring>
 #include <mutex>
 
@@ -52,7 +54,8 @@ constexpr size_t kOffStrong = al(kOffEdges + ((size_t)kNaMaxEdges + kNaMaxNodes)
 constexpr size_t kOffWeak = al(kOffStrong + (size_t)kNaMaxNodes * 4);
 constexpr size_t kScratchBytes = al(kOffWeak + (size_t)kNaMaxNodes * 4);
 
-// The scratch memory itself (about 7 MiB).
+// The scratch memory itself.
+static_assert(kScratchBytes == 6892032, "the stated size of the scratch array must follow its layout");
 static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
 
 // words at kOffWords

@@ -172,3 +172,45 @@ def test_plain_runs_after_serving_and_beside_other_block_shapes(orc):
         _same(wide.result(hw), ref, "served")
         assert wide.run(hw) == 0
         _same(wide.result(hw), ref, "after serving")
+
+
+def _request(i, n):
+    """The serving workload's request graph i (64 rounds, graph seed i), at a
+    chosen task count instead of the log-uniform draw."""
+    from workloads.graphs import _logu
+    st = Stream(i, 5)
+    _logu(st, 64, 262144)
+    return w.motif_graph(st, n, seed=i, rounds=64, name=f"request{i}")
+
+
+def test_full_size_requests_served_together_equal_oracle():
+    """Requests of the serving recipe up to its largest size (262,144 tasks,
+    64 rounds, 5 % loop conditions), admitted while the others run, each
+    equal to the oracle element by element; only the masked requests'
+    instances are kept."""
+    from paper_2004_10908_b300 import Executor
+    sizes = [262144, 64, 180000, 4096, 262144, 1000]
+    gs = [_request(100 + i, n) for i, n in enumerate(sizes)]
+    with Executor(arena_bytes=2 << 30) as ex2:
+        ts = [ex2.graph(g) for g in gs]
+        which = np.array([0, 1, 2, 3, 4, 5, 0, 2], np.uint32)
+        arrival = (np.arange(which.shape[0], dtype=np.uint64) * 20_000)   # 50k requests/s
+        mask = np.array([1, 1, 1, 1, 1, 1, 0, 1], bool)
+        ex2.serve_start(time_limit_ns=60_000_000_000)
+        try:
+            st, lat, sts, peak, kept = ex2.serve_replay(ts, which, arrival, keep=mask)
+        finally:
+            assert ex2.serve_stop() == 0
+        assert st == 0 and (sts == 0).all()
+        assert peak > 1
+        assert kept[6] is None
+        refs = {}
+        for r, wi in enumerate(which):
+            if not mask[r]:
+                continue
+            if wi not in refs:
+                refs[wi] = oracle.run(gs[wi])
+            _same(ex2.result(kept[r]), refs[wi], gs[wi].name)
+            kept[r].destroy()
+        for t in ts:
+            t.destroy()

@@ -94,3 +94,56 @@ def test_frozen_vectors(orc):
             assert orc.cond_hash(*vals[:3]) == vals[3]
         n += 1
     assert n >= 15
+
+
+def test_condition_hash_inverts_to_its_seed_constant(orc):
+    """HC(seed, id, iter) = L(L(L(seed ^ K) ^ id) ^ iter): undoing the three
+    mixes with the inverse mixer (written from the xorshift-multiply steps,
+    not from the oracle) and the three xors must give back K = 0xA511E9B3 for
+    any inputs.  A wrong nesting order, a swapped argument or a mistyped
+    constant fails this."""
+    rng = random.Random(11)
+    for _ in range(3000):
+        seed, tid, it = rng.getrandbits(32), rng.getrandbits(31), rng.getrandbits(20)
+        z = pins.mix32_inverse(orc.cond_hash(seed, tid, it)) ^ it
+        z = pins.mix32_inverse(z) ^ tid
+        z = pins.mix32_inverse(z) ^ seed
+        assert z == 0xA511E9B3
+
+
+def _np_mix32(x):
+    x = x.astype(np.uint32)
+    x ^= x >> np.uint32(16)
+    x *= np.uint32(0x7FEB352D)
+    x ^= x >> np.uint32(15)
+    x *= np.uint32(0x846CA68B)
+    x ^= x >> np.uint32(16)
+    return x
+
+
+def test_condition_hash_and_loop_exit_match_a_numpy_restatement(orc):
+    """The condition hash and the loop rule restated with numpy uint32
+    arithmetic, compared with the oracle on random inputs (including the exit
+    arm 1 + HC mod (nsucc - 1) of a loop with more than one exit)."""
+    rng = np.random.default_rng(19)
+    n = 4000
+    seed = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    tid = rng.integers(0, 1 << 31, n, dtype=np.uint64).astype(np.uint32)
+    it = rng.integers(0, 1 << 12, n, dtype=np.uint64).astype(np.uint32)
+    with np.errstate(over="ignore"):
+        hc = _np_mix32(_np_mix32(_np_mix32(seed ^ np.uint32(0xA511E9B3)) ^ tid) ^ it)
+    for i in range(n):
+        assert orc.cond_hash(int(seed[i]), int(tid[i]), int(it[i])) == int(hc[i])
+    trips = rng.integers(1, 17, n)
+    nsucc = rng.integers(2, 6, n)
+    for i in range(n):
+        T, k = int(trips[i]), int(nsucc[i])
+        if (int(it[i]) + 1) % T != 0:
+            want = 0
+        elif k <= 2:
+            want = 1
+        else:
+            want = 1 + int(hc[i]) % (k - 1)
+        assert orc.condition_index(2, 64 | (T << 16), int(seed[i]), int(tid[i]), int(it[i]), k) == want
+        # branch rule: HC mod nsucc
+        assert orc.condition_index(1, 64, int(seed[i]), int(tid[i]), int(it[i]), k) == int(hc[i]) % k
