@@ -341,6 +341,8 @@ typedef struct {
     uint64_t peak_thieves;     /* most blocks stealing at the same time (thief_mode 1) */
     uint64_t failed_rounds;    /* steal rounds (own deque, advertised victims, injection
                                   queue) that found nothing: the polling a thief policy wastes */
+    uint64_t round_cycles;     /* SM cycles those failed rounds took (e_s of the paper's bound
+                                  on wasteful steals = round_cycles / failed_rounds) */
 } tg_stats;
 int tg_ctx_get_stats(tg_ctx *ctx, tg_stats *st);
 int tg_ctx_get_opts(const tg_ctx *ctx, tg_ctx_opts *opts);
@@ -365,6 +367,13 @@ int tg_ctx_set_launch(tg_ctx *ctx, const tg_ctx_opts *launch);
  *    *ns = device time, *last = the final output. */
 int tg_bench_payload(tg_ctx *ctx, uint64_t count, uint32_t rounds, uint64_t *ns, uint32_t *checksum);
 int tg_bench_atomics(tg_ctx *ctx, uint64_t count, uint64_t footprint_words, uint64_t *ns);
+/*  tg_bench_payload_tasks: the payload alone over a given multiset of
+ *    executions (device arrays of n entries): task i runs cnt[i] payloads,
+ *    iterations 0..cnt[i]-1, of rounds[i] rounds on id ids[i], one thread
+ *    per task, so the arrays' order decides which executions share a warp;
+ *    *ns = device time, *checksum = XOR of all outputs. */
+int tg_bench_payload_tasks(tg_ctx *ctx, uint32_t n, const uint32_t *ids, const uint32_t *rounds,
+                           const uint32_t *cnt, uint64_t *ns, uint32_t *checksum);
 int tg_bench_chain(tg_ctx *ctx, uint32_t hops, uint32_t rounds, uint64_t *ns, uint32_t *last);
 
 /* Capturer baseline (Algorithm 1): a static DAG as one kernel per task,

@@ -59,7 +59,8 @@ class tg_stats(ctypes.Structure):
                  "spills", "idle_loops", "warp_iters", "pops_hand", "kernel_ns")] + \
                [("worker_blocks", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
                 ("phase_cycles", ctypes.c_uint64 * 5), ("parks", ctypes.c_uint64),
-                ("peak_thieves", ctypes.c_uint64), ("failed_rounds", ctypes.c_uint64)]
+                ("peak_thieves", ctypes.c_uint64), ("failed_rounds", ctypes.c_uint64),
+                ("round_cycles", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k == "phase_cycles" else getattr(self, k)) for k, _ in self._fields_}
@@ -104,6 +105,7 @@ SIGNATURES = {
                                          ctypes.POINTER(_u64)]),
     "tg_bench_payload": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "tg_bench_atomics": (ctypes.c_int, [_vp, _u64, _u64, ctypes.POINTER(_u64)]),
+    "tg_bench_payload_tasks": (ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "tg_bench_chain": (ctypes.c_int, [_vp, _u32, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "tg_levelize": (ctypes.c_int, [_u32, _u32, _vp, _vp, _vp, _vp, ctypes.POINTER(_u32)]),
     "tg_stream_plan": (ctypes.c_int, [_u32, _u32, _vp, _vp, _u32, _vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
@@ -392,6 +394,16 @@ def tg_bench_chain(ctx, hops, rounds):
     last = _u32(0)
     _check(load().tg_bench_chain(_vp(ctx), hops, rounds, ctypes.byref(ns), ctypes.byref(last)), "tg_bench_chain")
     return ns.value, last.value
+
+
+def tg_bench_payload_tasks(ctx, n, ids_ptr, rounds_ptr, cnt_ptr):
+    """Returns (device ns, checksum) of the payloads of a given execution
+    multiset (device arrays of n uint32 each; see include/tg.h)."""
+    ns = _u64(0)
+    cs = _u32(0)
+    _check(load().tg_bench_payload_tasks(_vp(ctx), n, _vp(ids_ptr), _vp(rounds_ptr), _vp(cnt_ptr), ctypes.byref(ns),
+                                         ctypes.byref(cs)), "tg_bench_payload_tasks")
+    return ns.value, cs.value
 
 
 def tg_bench_atomics(ctx, count, footprint_words):

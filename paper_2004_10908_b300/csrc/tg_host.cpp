@@ -521,10 +521,14 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
     return TG_OK;
 }
 
+int tg_serve_stop(tg_ctx *c);
+
 int tg_ctx_destroy(tg_ctx *c)
 {
     if (!c)
         return TG_ERR_INVALID;
+    if (c->serving)
+        tg_serve_stop(c);   // a resident scheduler would otherwise run to its time limit
     cudaStreamSynchronize(c->stream);
     for (auto &kv : c->subs)
         if (kv.second.ev)
@@ -1992,6 +1996,7 @@ int tg_ctx_get_stats(tg_ctx *c, tg_stats *st)
             st->phase_cycles[i] += s[ST_PHASE0 + i];
         st->parks += s[ST_PARK];
         st->failed_rounds += s[ST_FAILED_ROUND];
+        st->round_cycles += s[ST_ROUND_CYCLES];
         st->peak_thieves = std::max<uint64_t>(st->peak_thieves, s[ST_PEAK_THIEVES]);
     }
     if (c->timed) {
@@ -2011,6 +2016,27 @@ int tg_bench_payload(tg_ctx *c, uint64_t count, uint32_t rounds, uint64_t *ns, u
     TG_CUDA(cudaMemsetAsync(c->scratch, 0, 4, c->stream));
     TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
     TG_CUDA(launch_bench_payload(count, rounds, c->scratch, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    u32 cs = 0;
+    TG_CUDA(cudaMemcpyAsync(&cs, c->scratch, 4, cudaMemcpyDeviceToHost, c->stream));
+    TG_CUDA(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    TG_CUDA(cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1));
+    *ns = (u64)((double)ms * 1e6);
+    if (checksum)
+        *checksum = cs;
+    c->timed = false;
+    return TG_OK;
+}
+
+int tg_bench_payload_tasks(tg_ctx *c, uint32_t n, const uint32_t *ids, const uint32_t *rounds, const uint32_t *cnt,
+                           uint64_t *ns, uint32_t *checksum)
+{
+    if (!c || !ns || (n && (!ids || !rounds || !cnt)))
+        return TG_ERR_INVALID;
+    TG_CUDA(cudaMemsetAsync(c->scratch, 0, 4, c->stream));
+    TG_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    TG_CUDA(launch_bench_payload_tasks(n, ids, rounds, cnt, c->scratch, c->stream));
     TG_CUDA(cudaEventRecord(c->ev_k1, c->stream));
     u32 cs = 0;
     TG_CUDA(cudaMemcpyAsync(&cs, c->scratch, 4, cudaMemcpyDeviceToHost, c->stream));

@@ -97,7 +97,7 @@ struct alignas(128) LaunchCtl {
 enum StatIdx {
     ST_TASKS = 0, ST_POP_LOCAL, ST_POP_OWN, ST_STEAL_TRY, ST_STEAL_HIT, ST_INJECT,
     ST_SPILL, ST_IDLE, ST_ITERS, ST_HAND, ST_PHASE0,   // ST_PHASE0 .. +4: traced cycles
-    ST_PARK = ST_PHASE0 + 5, ST_PEAK_THIEVES, ST_FAILED_ROUND, ST_COUNT = 24
+    ST_PARK = ST_PHASE0 + 5, ST_PEAK_THIEVES, ST_FAILED_ROUND, ST_ROUND_CYCLES, ST_COUNT = 24
 };
 
 constexpr u32 kEmpty32 = 0xFFFFFFFFu;
@@ -170,6 +170,8 @@ cudaError_t launch_clear(u64 *slots, size_t count, cudaStream_t st);
 cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bool serve = false);
 size_t sched_dyn_smem(u32 smem_entries, u32 warps);
 cudaError_t launch_bench_payload(u64 count, u32 rounds, u32 *checksum, cudaStream_t st);
+cudaError_t launch_bench_payload_tasks(u32 n, const u32 *ids, const u32 *rounds, const u32 *cnt, u32 *checksum,
+                                       cudaStream_t st);
 cudaError_t launch_bench_atomics(u64 *words, u64 footprint, u64 count, u64 *sink, cudaStream_t st);
 cudaError_t launch_bench_chain(u32 hops, u32 rounds, u32 *last, cudaStream_t st);
 // Fresh records for an instance: the immutable half of the template's records

@@ -503,6 +503,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     u32 st_tasks = 0, st_local = 0, st_own = 0, st_try = 0, st_hit = 0, st_inj = 0, st_spill = 0,
         st_iters = 0, st_hand = 0, st_park = 0, st_fail = 0;
     u64 st_idle = 0;
+    u64 st_rcyc = 0, r_t0 = 0;   // SM cycles of the steal rounds that found nothing (lane 0)
     // adaptive thieves (Alg. 3/6 invariant): a block is active while one of
     // its warps executes; blocks are the workers whose counts are kept
     const bool adaptive = !kServe && kExt && p.thief_mode == 1u;
@@ -599,6 +600,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                         backoff = min(backoff * 2u, 4096u);
                     continue;
                 }
+                if (lane == 0)
+                    r_t0 = clock64();
                 if (kServe) {
                     // claim the next submitted graph, re-arm its pending
                     // count and status, and take its sources (Algorithm 8)
@@ -718,6 +721,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                     // stop when every graph is done, on abort, timeout or cancel
                     st_idle++;
                     st_fail++;
+                    if (lane == 0)
+                        st_rcyc += clock64() - r_t0;
                     int stop = 0;
                     if (lane == 0) {
                         bool done = kServe ? (vld32(&p.ctl->stop) != 0u) : (vld32(&p.ctl->graphs_left) == 0u);
@@ -1364,6 +1369,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         atomicAdd(&s_stats[ST_HAND], st_hand);
         atomicAdd(&s_stats[ST_PARK], st_park);
         atomicAdd(&s_stats[ST_FAILED_ROUND], st_fail);
+        atomicAdd(&s_stats[ST_ROUND_CYCLES], st_rcyc);
     }
     // tasks are counted per lane
     atomicAdd(&s_stats[ST_TASKS], st_tasks);
@@ -1552,6 +1558,24 @@ __global__ void bench_payload_kernel(u64 count, u32 rounds, u32 *checksum)
         atomicXor(checksum, acc);
 }
 
+// The payload alone over a given multiset of executions: thread i runs task
+// i's cnt[i] payloads (iterations 0..cnt[i]-1) of rounds[i] rounds on id
+// ids[i].  The arrays' order decides which executions share a warp.
+__global__ void bench_payload_tasks_kernel(u32 n, const u32 *ids, const u32 *rounds, const u32 *cnt, u32 *checksum)
+{
+    u32 acc = 0;
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const u32 id = ids[i], R = rounds[i], c = cnt[i];
+        for (u32 it = 0; it < c; ++it)
+            acc ^= task_payload(id, it, 0u, R);
+    }
+    for (int o = 16; o; o >>= 1)
+        acc ^= __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0)
+        atomicXor(checksum, acc);
+}
+
 // The compute along a path of `hops` dependent tasks, with nothing else.
 __global__ void bench_chain_kernel(u32 hops, u32 rounds, u32 *last)
 {
@@ -1710,6 +1734,15 @@ cudaError_t launch_bench_payload(u64 count, u32 rounds, u32 *checksum, cudaStrea
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     bench_payload_kernel<<<sms * 8, 256, 0, st>>>(count, rounds, checksum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bench_payload_tasks(u32 n, const u32 *ids, const u32 *rounds, const u32 *cnt, u32 *checksum,
+                                       cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    bench_payload_tasks_kernel<<<(n + 255u) / 256u, 256, 0, st>>>(n, ids, rounds, cnt, checksum);
     return cudaGetLastError();
 }
 

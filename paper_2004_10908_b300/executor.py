@@ -163,6 +163,15 @@ class Executor:
     def bench_payload(self, count, rounds):
         return B.tg_bench_payload(self.ctx, count, rounds)
 
+    def bench_payload_tasks(self, ids, rounds, cnt):
+        """Payload-only time of an execution multiset given as host arrays
+        (task ids, rounds, execution counts), in the arrays' order."""
+        t = self.torch
+        dev = [t.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda() for a in (ids, rounds, cnt)]
+        out = B.tg_bench_payload_tasks(self.ctx, len(ids), *(d.data_ptr() for d in dev))
+        del dev
+        return out
+
     def bench_atomics(self, count, footprint_words):
         return B.tg_bench_atomics(self.ctx, count, footprint_words)
 

@@ -239,6 +239,42 @@ def test_adaptive_thieves_parity_and_fewer_wasted_steals():
     assert wasted[1] * 4 < wasted[0], wasted
 
 
+def test_wasteful_steals_within_the_papers_bound():
+    """The paper's bound on wasteful steals (Analysis, third theorem): at any
+    moment at most MAX_STEALS x (|W| + |D| E / e_s) of them, W the workers
+    (here worker blocks), one domain, E the longest task, e_s one steal
+    round.  Counted in rounds over windows of length E, a run of length T
+    wastes at most (|W| + E / e_s) x ceil(T / E) rounds.  E is measured as
+    one payload of the chain's tasks, e_s from the device's own count of the
+    cycles its failed rounds took.  Checked for both thief modes on the worst
+    case the proof names (one task ready at a time: a chain) and on a wide
+    layered DAG."""
+    import math
+
+    import torch
+    from paper_2004_10908_b300 import Executor
+    from workloads.graphs import STATIC, from_lists, pack_param
+    try:
+        mhz = float(torch.cuda.clock_rate(0)) or 2032.0
+    except Exception:   # noqa: BLE001 -- no clock query available: the maximum clock
+        mhz = 2032.0
+    R = 64
+    chain = from_lists("chain", [STATIC] * 2000, [pack_param(R)] * 2000, [(i, i + 1) for i in range(1999)])
+    wide = w.config2a(seed=5, levels=60, width=500, rounds=R)
+    for mode in (0, 1):
+        with Executor(arena_bytes=1 << 29, thief_mode=mode) as ex:
+            E_ns = ex.bench_chain(200, R)[0] / 200.0
+            for g in (chain, wide):
+                h = ex.graph(g)
+                assert ex.run(h) == 0
+                s = ex.stats()
+                h.destroy()
+                failed, cyc = s["failed_rounds"], s["round_cycles"]
+                assert failed > 0 and cyc > 0
+                e_s_ns = cyc / failed / (mhz * 1e-3)
+                bound = (s["worker_blocks"] + E_ns / e_s_ns) * math.ceil(s["kernel_ns"] / E_ns)
+                assert failed <= bound, (mode, g.name, failed, bound, E_ns, e_s_ns)
+
 
 def test_adaptive_thieves_finish_a_wide_wavefront():
     """Adaptive thieves with a short local backlog on a wide wavefront: busy
