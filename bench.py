@@ -750,7 +750,7 @@ def serving(Executor, torch):
     # pools sized for every request graph resident at once (about 637 M task
     # slots) plus the instances kept for checking (5,000 at 1k req/s, about
     # 160 M) and those in flight; the 64 GB budget covers all of them
-    with Executor(arena_bytes=(2 << 30) if SMALL else (58 << 30), max_nodes=0 if SMALL else 850_000_000,
+    with Executor(arena_bytes=(8 << 30) if SMALL else (58 << 30), max_nodes=0 if SMALL else 850_000_000,
                   max_edges=0 if SMALL else 2_600_000_000, mem_budget_bytes=64 << 30) as ex:
         t0 = time.perf_counter()
         ts, n_tasks, n_edges, n_exec, pack_ns, up_ns = [], [], [], [], [], []

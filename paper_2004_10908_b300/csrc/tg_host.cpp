@@ -2198,6 +2198,8 @@ int tg_serve_start(tg_ctx *c, uint64_t time_limit_ns)
     TG_CUDA(cudaMemsetAsync(c->dqc, 0, (size_t)kMaxBlocks * sizeof(QCtr), c->stream));
     TG_CUDA(cudaMemsetAsync(c->thief_slots, 0, (size_t)1024 * 128, c->stream));
     TG_CUDA(cudaMemsetAsync(c->stats, 0, (size_t)kMaxBlocks * ST_COUNT * sizeof(u64), c->stream));
+    TG_CUDA(preload_serving_kernels(c->side));
+    TG_CUDA(cudaStreamSynchronize(c->side));
     TG_CUDA(cudaStreamSynchronize(c->stream));
     KParams p = base_params(c, g);
     p.lt = nullptr;

@@ -178,6 +178,11 @@ cudaError_t launch_bench_chain(u32 hops, u32 rounds, u32 *last, cudaStream_t st)
 // at src_off (successor range, degrees, kind, parameters, id), join word =
 // strong in-degree, count = digest = 0, written at dst_off (may equal src_off).
 cudaError_t launch_instance_rearm(NodeSlot *slots, u64 src_off, u64 dst_off, u32 n, cudaStream_t st);
+// Launch, once and with no work, every kernel the host may launch while the
+// resident server runs, so that none of them is loaded for the first time
+// then: with lazy module loading a first launch waits for the running
+// kernel, which waits for that launch's work -- until its time limit.
+cudaError_t preload_serving_kernels(cudaStream_t st);
 cudaError_t launch_capture_task(NodeSlot *slots, u32 *outv, const u32 *edges, u32 u, u32 node_off, cudaStream_t st);
 // tg_result.cu: pack the count and digest of tasks [node_off, node_off + n) into dst[0, n)
 cudaError_t launch_result_gather(const NodeSlot *slots, u32 node_off, u32 n, u64 *dst, cudaStream_t st);

@@ -1770,6 +1770,12 @@ cudaError_t launch_instance_rearm(NodeSlot *slots, u64 src_off, u64 dst_off, u32
     return cudaGetLastError();
 }
 
+cudaError_t preload_serving_kernels(cudaStream_t st)
+{
+    instance_rearm_kernel<<<1, 32, 0, st>>>(nullptr, 0ull, 0ull, 0u);   // n = 0: touches nothing
+    return cudaGetLastError();
+}
+
 cudaError_t launch_capture_task(NodeSlot *slots, u32 *outv, const u32 *edges, u32 u, u32 node_off, cudaStream_t st)
 {
     capture_task_kernel<<<1, 32, 0, st>>>(slots, outv, edges, u, node_off);

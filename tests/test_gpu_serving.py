@@ -214,3 +214,41 @@ def test_full_size_requests_served_together_equal_oracle():
             kept[r].destroy()
         for t in ts:
             t.destroy()
+
+
+def test_serving_first_thing_in_a_fresh_process():
+    """A process whose first launches are the server's: the kernels the host
+    launches while the resident scheduler runs are loaded before it starts
+    (with lazy module loading a first launch would wait for the running
+    server, which waits for that launch -- until its time limit).  The run
+    is bounded by a 20 s server limit and a 180 s process timeout."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import numpy as np, sys
+sys.path.insert(0, sys.argv[1])
+import workloads as w, oracle
+from workloads.rng import Stream
+from paper_2004_10908_b300 import Executor
+st = Stream(7, 9)
+gs = [w.motif_graph(st, 3000 + 500 * i, seed=70 + i, rounds=16) for i in range(3)]
+with Executor(arena_bytes=1 << 29) as ex:
+    ts = [ex.graph(g) for g in gs]
+    ex.serve_start(time_limit_ns=20_000_000_000)
+    try:
+        rc, lat, sts, peak, kept = ex.serve_replay(ts, np.array([0, 1, 2, 1], np.uint32),
+                                                   np.arange(4, dtype=np.uint64) * 1000, keep=True)
+    finally:
+        stop = ex.serve_stop()
+    assert rc == 0 and stop == 0 and (sts == 0).all(), (rc, stop, list(sts))
+    for r, wi in enumerate([0, 1, 2, 1]):
+        out, cnt, dig, _ = ex.result(kept[r])
+        ref = oracle.run(gs[wi])
+        assert (out == ref.out).all() and (cnt == ref.cnt).all() and (dig == ref.dig).all()
+        kept[r].destroy()
+print("served")
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "-c", code, root], capture_output=True, text=True, timeout=180)
+    assert res.returncode == 0 and "served" in res.stdout, res.stdout[-2000:] + res.stderr[-2000:]
