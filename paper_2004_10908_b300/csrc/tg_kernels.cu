@@ -375,6 +375,22 @@ __device__ __forceinline__ u64 settle_finish(const KParams &p, bool &pend, u64 o
     return cont;
 }
 
+// A load that stays where it is written (the compiler may not sink it
+// towards its first use): issued before the payload, its latency hides
+// under it.  Predicated: with `pred` false nothing is read and 0 returned.
+template <bool kServe>
+__device__ __forceinline__ u32 ld_early(const u32 *ptr, bool pred)
+{
+    u32 v = 0;
+    if (kServe)
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.cg.u32 %0, [%1];\n\t}"
+                     : "+r"(v) : "l"(ptr), "r"((u32)pred));
+    else
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.u32 %0, [%1];\n\t}"
+                     : "+r"(v) : "l"(ptr), "r"((u32)pred));
+    return v;
+}
+
 // Loads of data that is immutable while its graph exists: through L1 for a
 // one-shot launch; through L2 for the resident server, whose node ranges and
 // graph slots are recycled while it runs.
@@ -908,7 +924,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             for (int j = 0; j < kRelUnroll; ++j) {
                 v_[j] = j0 + (u32)j < c;
                 ow_[j] = (u32)lane;
-                s_[j] = v_[j] ? ld_imm<kServe>(&p.edges[succ_off + j0 + (u32)j]) : 0u;
+                s_[j] = ld_early<kServe>(&p.edges[succ_off + j0 + (u32)j], v_[j]);
             }
         };
         // (the base of the owner's graph: an idle lane may own no graph)
@@ -935,7 +951,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 const u32 off_o = __shfl_sync(kFull, succ_off, o);
                 const u32 ex_o = __shfl_sync(kFull, excl, o);
                 ow_[j] = (u32)o;
-                s_[j] = v_[j] ? ld_imm<kServe>(&p.edges[off_o + (eq - ex_o)]) : 0u;
+                s_[j] = ld_early<kServe>(&p.edges[off_o + (eq - ex_o)], v_[j]);
             }
         };
         if (per_lane) {
@@ -961,7 +977,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         if (!kAcyc && act && c_status == 0 && kind >= TG_COND_BRANCH && kind <= TG_COND_CONST) {
             c_r = cond_index(kind, arg, c_seed, lid, iter, succ_cnt);
             if (c_r >= 0 && (u32)c_r < succ_cnt)
-                c_raw = ld_imm<kServe>(&p.edges[succ_off + (u32)c_r]);
+                c_raw = ld_early<kServe>(&p.edges[succ_off + (u32)c_r], true);
             else
                 c_r = -1;
         }
