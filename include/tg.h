@@ -218,21 +218,25 @@ int tg_poll(tg_ctx *ctx, uint64_t ticket);
 int tg_wait(tg_ctx *ctx, uint64_t ticket);
 
 /* Make another execution instance of graph g: its own task state, outputs
- * and graph slot, sharing g's packed successor lists (no host packing, no
- * kernel: copy-engine copies on a side stream).  Several instances of one
+ * and graph slot, sharing g's packed successor lists (no host packing: a
+ * small kernel on a side stream copies the immutable half of g's task
+ * records and sets the fresh state).  Several instances of one
  * graph may run at the same time.  Destroy it with tg_graph_destroy; g cannot
  * be destroyed while it has instances (TG_ERR_BUSY).  TG_ERR_BUDGET if the
  * memory budget or the pools cannot hold it. */
 int tg_instance_create(tg_ctx *ctx, tg_graph *g, tg_graph **out);
 
-/* Serving (continuous batching): start a resident scheduler on the context
- * stream.  While it runs, tg_submit queues a graph (or instance) through a
- * device submission ring -- its task state is re-armed by a copy-engine copy
- * and the resident kernel injects its sources while other graphs are running
+/* Serving (continuous batching; the paper's co-run experiments run many
+ * task graphs on one executor at once): start a resident scheduler on the
+ * context stream.  While it runs, tg_submit queues a graph (or instance)
+ * through a device submission ring -- its task state is re-armed by a small
+ * kernel on the side stream (loaded before the server starts, so that its
+ * first launch never waits for the running server) and the resident kernel
+ * injects its sources while other graphs are running
  * -- and tg_poll / tg_wait read the completion records the kernel posts to
  * host-mapped memory.  tg_run and batches return TG_ERR_BUSY meanwhile.
  * The server runs one block per SM, with the context's warps per block
- * halved until two such blocks would fit on an SM, so that the copy kernels
+ * halved until two such blocks would fit on an SM, so that the kernels
  * re-arming instances can run beside it.
  * time_limit_ns bounds the server's lifetime (0 = 60 s); a graph still in
  * flight at the limit ends with TG_ERR_TIMEOUT.  Admission by memory budget

@@ -2174,7 +2174,7 @@ int tg_serve_start(tg_ctx *c, uint64_t time_limit_ns)
         return rc;
     Geometry g = c->geo;
     // one block per SM, of a shape of which two would fit: the resident
-    // server leaves room on every SM for the copy kernels that re-arm
+    // server leaves room on every SM for the kernels that re-arm
     // instances (device-to-device record copies)
     int per_sm = 0;
     for (;;) {
