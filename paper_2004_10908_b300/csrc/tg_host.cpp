@@ -2175,7 +2175,7 @@ int tg_serve_start(tg_ctx *c, uint64_t time_limit_ns)
     Geometry g = c->geo;
     // one block per SM, of a shape of which two would fit: the resident
     // server leaves room on every SM for the kernels that re-arm
-    // instances (device-to-device record copies)
+    // instances (their records from the template's immutable half)
     int per_sm = 0;
     for (;;) {
         if (sched_occupancy(g.threads, sched_dyn_smem(g.ring, (u32)(g.threads / 32)), &per_sm, true) !=
