@@ -219,7 +219,8 @@ def headline(ex, graphs, args, torch, B, world=1):
     for h, g in zip(handles, graphs):
         chosen, _ = ex.autotune(h, trials=2, cache_path=TUNE_CACHE)
         tuned[g.name] = {k: chosen[k] for k in ("worker_blocks", "warps_per_block", "batch_max", "local_keep",
-                                                "max_thieves", "thief_mode", "steal_policy", "max_steal")}
+                                                "max_thieves", "thief_mode", "steal_policy", "max_steal",
+                                                "steal_backoff_ns", "idle_sleep_ns")}
     tuned["autotune_s"] = time.perf_counter() - t0
 
     def step():
@@ -681,7 +682,8 @@ def batched(Executor, torch):
             "mean_rounds": rounds / execs,
             "oracle_checked_graphs": checked, "oracle_match": ok,
             "autotuned": {k: chosen[k] for k in ("worker_blocks", "warps_per_block", "deque_depth",
-                                                 "steal_policy", "max_steal", "max_thieves")},
+                                                 "steal_policy", "max_steal", "max_thieves", "batch_max",
+                                                 "local_keep", "steal_backoff_ns", "idle_sleep_ns")},
             "autotune_s": tune_s, "generate_s": gen_s,
             "cpu_all_cores": oracle_all_cores(gs[::8], "every 8th graph of the batch")}
 

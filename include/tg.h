@@ -131,6 +131,11 @@ typedef struct {
     uint64_t mem_budget_bytes; /* admission budget for graph memory [the node/edge pools] */
     uint64_t max_nodes;        /* node pool capacity [derived from the arena] */
     uint64_t max_edges;        /* edge pool capacity [derived from the arena] */
+    uint32_t steal_backoff_ns; /* longest sleep of a thief between steal rounds that found
+                                  nothing: it doubles from 256 ns up to this.  Short sleeps
+                                  find spilled work sooner on wide graphs; long ones leave
+                                  the memory system to the busy warps of a long chain
+                                  (at most 1,000,000) [512] */
 } tg_ctx_opts;
 
 /* Create a context on the current CUDA device.
@@ -293,8 +298,9 @@ int tg_batch_launch(tg_ctx *ctx, tg_batch *b);
 int tg_batch_wait(tg_ctx *ctx, tg_batch *b, int *statuses);
 int tg_batch_destroy(tg_ctx *ctx, tg_batch *b);
 /* Autotune a batch (worker-block count, warps per block, deque depth, steal
- * policy, victims per steal round, thief slots, activations per warp step):
- * time its launch under
+ * policy, victims per steal round, thief slots, activations per warp step,
+ * local backlog, thief mode, a thief's longest sleep and an idle warp's
+ * sleep): time its launch under
  * candidate geometries by coordinate descent, `trials` timed launches each,
  * keep the fastest and re-capture the batch with it.  With cache_path
  * non-NULL, a result cached for the same device and batch shape (graph,
@@ -305,8 +311,7 @@ int tg_batch_destroy(tg_ctx *ctx, tg_batch *b);
 int tg_batch_autotune(tg_ctx *ctx, tg_batch *b, uint32_t trials, const char *cache_path,
                       tg_ctx_opts *chosen, uint64_t *best_ns);
 
-/* Autotune one graph's launch geometry (the batch knobs above plus
- * activations per step, local backlog and thief mode) by timing real runs
+/* Autotune one graph's launch geometry (the batch knobs above) by timing real runs
  * of it: `trials` timed runs per candidate after one warm-up, coordinate
  * descent, the winner cached under the device and graph shape in
  * cache_path (NULL: no cache).  The graph keeps the chosen geometry for its
@@ -353,7 +358,8 @@ int tg_ctx_get_opts(const tg_ctx *ctx, tg_ctx_opts *opts);
 /* Change the launch geometry used by later single-graph launches and by
  * batches created afterwards.  Reads worker_blocks, warps_per_block,
  * deque_depth (at most the context's), steal_policy, max_steal, smem_ring,
- * idle_sleep_ns and max_thieves (0 = default); other fields are ignored.
+ * idle_sleep_ns, max_thieves, batch_max, local_keep, thief_mode and
+ * steal_backoff_ns (0 = default); other fields are ignored.
  * TG_ERR_INVALID if a field is out of range or the block shape cannot be
  * resident. */
 int tg_ctx_set_launch(tg_ctx *ctx, const tg_ctx_opts *launch);

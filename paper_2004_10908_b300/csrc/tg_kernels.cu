@@ -529,6 +529,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     u64 pend_old = 0, pend_delta = 0;
     u32 pend_g = 0, pend_cap = 0;
     u32 backoff = 256;
+    const u32 backoff_max = p.steal_backoff_ns ? p.steal_backoff_ns : 512u;
     const u32 my_slot = blockIdx.x % p.max_thieves;
     u32 idle = 0;
     u32 noslot = 0;
@@ -613,7 +614,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                     }
                     __nanosleep(am == 2 ? backoff : p.idle_sleep_ns);
                     if (am == 2)
-                        backoff = min(backoff * 2u, 4096u);
+                        backoff = min(backoff * 2u, backoff_max);
                     continue;
                 }
                 if (lane == 0)
@@ -821,7 +822,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                         break;
                     idle++;
                     __nanosleep(backoff);
-                    backoff = min(backoff * 2u, 4096u);
+                    backoff = min(backoff * 2u, backoff_max);
                     continue;
                 }
                 if (lane == 0) {

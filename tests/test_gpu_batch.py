@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import workloads as w
+from paper_2004_10908_b300 import binding as B
 
 pytestmark = pytest.mark.gpu
 
@@ -117,6 +118,8 @@ def test_launch_geometry_variants_are_exact(ex):
     try:
         for geo in (dict(warps_per_block=4, worker_blocks=148, steal_policy=1, max_steal=2, max_thieves=4),
                     dict(warps_per_block=16, deque_depth=256, max_thieves=64),
+                    dict(steal_backoff_ns=4096, idle_sleep_ns=1024),
+                    dict(steal_backoff_ns=32, worker_blocks=296, warps_per_block=8),
                     dict(worker_blocks=1, warps_per_block=1)):
             ex.set_launch(**geo)
             b = ex.batch(hs)
@@ -125,6 +128,8 @@ def test_launch_geometry_variants_are_exact(ex):
             assert st == 0, geo
             _check_against_oracle(ex, gs, hs)
             b.destroy()
+        with pytest.raises(B.TgError):
+            ex.set_launch(steal_backoff_ns=1_000_001)   # above the documented limit
     finally:
         ex.set_launch()
         for h in hs:
