@@ -1779,8 +1779,8 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
     const int policy_c[] = {0, 1};
     const int steal_c[] = {2, 8, 32};
     const int thief_c[] = {8, 16, 64};
-    const int batch_c[] = {8, 16, 32};
-    const int keep_c[] = {16, 32, 128, 512};
+    const int batch_c[] = {8, 16, 24, 32};
+    const int keep_c[] = {16, 32, 64, 128, 512};
     const int tmode_c[] = {0, 1};
     const int backoff_c[] = {512, 4096};
     const int idle_c[] = {256, 1024};
@@ -1807,18 +1807,25 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
         }
         return TG_OK;
     };
-    if ((rc = try_knob([](tg_ctx_opts &o, int v) { o.warps_per_block = v; o.worker_blocks = 0; }, warps_c, 3)) != TG_OK ||
-        (rc = try_knob([&](tg_ctx_opts &o, int v) { o.worker_blocks = v * c->sm_count; }, bpsm_c, 3)) != TG_OK ||
-        (rc = try_knob([](tg_ctx_opts &o, int v) { o.deque_depth = v; }, depth_c, 2)) != TG_OK ||
-        (rc = try_knob([](tg_ctx_opts &o, int v) { o.steal_policy = v; }, policy_c, 2)) != TG_OK ||
-        (rc = try_knob([](tg_ctx_opts &o, int v) { o.max_steal = v; }, steal_c, 3)) != TG_OK ||
-        (rc = try_knob([](tg_ctx_opts &o, int v) { o.max_thieves = v; }, thief_c, 3)) != TG_OK ||
-        (rc = try_knob([](tg_ctx_opts &o, int v) { o.batch_max = v; }, batch_c, 3)) != TG_OK ||
-        (rc = try_knob([](tg_ctx_opts &o, int v) { o.local_keep = v; }, keep_c, 4)) != TG_OK ||
-        (rc = try_knob([](tg_ctx_opts &o, int v) { o.thief_mode = v; }, tmode_c, 2)) != TG_OK ||
-        (rc = try_knob([](tg_ctx_opts &o, int v) { o.steal_backoff_ns = (u32)v; }, backoff_c, 2)) != TG_OK ||
-        (rc = try_knob([](tg_ctx_opts &o, int v) { o.idle_sleep_ns = (u32)v; }, idle_c, 2)) != TG_OK)
-        return rc;
+    // the knobs interact (a larger batch wants a longer backlog), so a pass
+    // that improved on the start is followed by one more
+    for (int pass = 0; pass < 2; ++pass) {
+        const u64 pass_t = best_t;
+        if ((rc = try_knob([](tg_ctx_opts &o, int v) { o.warps_per_block = v; o.worker_blocks = 0; }, warps_c, 3)) != TG_OK ||
+            (rc = try_knob([&](tg_ctx_opts &o, int v) { o.worker_blocks = v * c->sm_count; }, bpsm_c, 3)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.deque_depth = v; }, depth_c, 2)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.steal_policy = v; }, policy_c, 2)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.max_steal = v; }, steal_c, 3)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.max_thieves = v; }, thief_c, 3)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.batch_max = v; }, batch_c, 4)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.local_keep = v; }, keep_c, 5)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.thief_mode = v; }, tmode_c, 2)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.steal_backoff_ns = (u32)v; }, backoff_c, 2)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.idle_sleep_ns = (u32)v; }, idle_c, 2)) != TG_OK)
+            return rc;
+        if (best_t >= pass_t)
+            break;
+    }
     if (cache_path) {
         if (FILE *f = std::fopen(cache_path, "a")) {
             std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %d %d %d %u %llu\n", key.c_str(), best.worker_blocks,

@@ -1016,17 +1016,12 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             if (lane == 0 && sumU)
                 atomicAdd(&p.descs[p.single_gid].pe, (u64)sumU);
         } else {
-            u32 rem = __ballot_sync(kFull, run);
-            while (rem) {
-                int l = __ffs(rem) - 1;
-                u32 g = __shfl_sync(kFull, gid, l);
-                bool in = run && gid == g;
-                u32 m = __ballot_sync(kFull, in);
-                u32 sumU = __reduce_add_sync(kFull, in ? U : 0u);
-                if (lane == l && sumU)
-                    atomicAdd(&p.descs[g].pe, (u64)sumU);
-                rem &= ~m;
-            }
+            // lanes grouped by graph (lanes that run nothing form one more
+            // group); each group's lowest lane adds the group's sum
+            const u32 m = __match_any_sync(kFull, run ? gid : kEmpty32);
+            const u32 sumU = __reduce_add_sync(m, U);
+            if (run && sumU && lane == __ffs(m) - 1)
+                atomicAdd(&p.descs[gid].pe, (u64)sumU);
         }
         if (run && !cont)
             st_tasks++;
@@ -1327,26 +1322,21 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                     }
                 }
             } else {
-                u32 rem = __ballot_sync(kFull, act);
-                while (rem) {
-                    int l = __ffs(rem) - 1;
-                    u32 g = __shfl_sync(kFull, gid, l);
-                    bool in = act && gid == g;
-                    u32 m = __ballot_sync(kFull, in);
-                    // a continuation consumes its pending count but is no execution
-                    u32 mx = __ballot_sync(kFull, in && !cont);
-                    u32 sumP = __reduce_add_sync(kFull, in ? P : 0u);
-                    u32 sumU = __reduce_add_sync(kFull, in ? U : 0u);
-                    if (lane == l) {
-                        const u32 E = (u32)__popc(m);
-                        const long long d = (long long)sumP - (long long)sumU - (long long)E;
-                        pend_delta = ((u64)__popc(mx) << 32) + (u64)d;
-                        pend_old = atomicAdd(&p.descs[g].pe, pend_delta);
-                        pend_g = g;
-                        pend_cap = c_cap;
-                        pend = true;
-                    }
-                    rem &= ~m;
+                // one pending-count update per graph of the step, by the
+                // lowest lane of the graph's group (as for the reservation)
+                const u32 m = __match_any_sync(kFull, act ? gid : kEmpty32);
+                // a continuation consumes its pending count but is no execution
+                const u32 mx = __ballot_sync(kFull, act && !cont) & m;
+                const u32 sumP = __reduce_add_sync(m, P);
+                const u32 sumU = __reduce_add_sync(m, U);
+                if (act && lane == __ffs(m) - 1) {
+                    const u32 E = (u32)__popc(m);
+                    const long long d = (long long)sumP - (long long)sumU - (long long)E;
+                    pend_delta = ((u64)__popc(mx) << 32) + (u64)d;
+                    pend_old = atomicAdd(&p.descs[gid].pe, pend_delta);
+                    pend_g = gid;
+                    pend_cap = c_cap;
+                    pend = true;
                 }
             }
         }
