@@ -345,6 +345,9 @@ def plain_single_graph(Executor, torch, B):
             e1.record(ex.stream)
             assert st == 0 and ex.wait(tk) == 0
             wall.append((time.perf_counter() - t1) * 1e6)
+            # the ticket completes when the run's status reaches the host,
+            # which can be before the stream has passed the end event
+            e1.synchronize()
             dev.append(e0.elapsed_time(e1) * 1e3)
             kern.append(ex.stats()["kernel_ns"] / 1e3)
         ok = _same_as_oracle(ex.result(h), ref)
@@ -513,6 +516,7 @@ def capturer_baseline(Executor, torch, B):
                 st, t = B.tg_submit(ex.ctx, h.handle)
                 e1.record(ex.stream)
                 assert st == 0 and ex.wait(t) == 0
+                e1.synchronize()
                 ts.append(e0.elapsed_time(e1))
             ref = ex.result(h)
             row = {"graph": f"layered {g.meta['levels']} x {g.meta['width']}, R={int(g.params[0] & 0xFFFF)}",
@@ -640,6 +644,7 @@ def batched(Executor, torch):
             e1.record(ex.stream)
             st, sts = b.wait()
             assert st == 0
+            e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         # the payload-only ceiling on the identical multiset of (id, iter,
         # rounds) the launch executed: in task order (lanes mixing rounds
