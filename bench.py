@@ -21,6 +21,9 @@ Measured in the same run and reported beside it:
             fractions, the oracle on one core; checked against the oracle
   thief_policies  capped vs adaptive thieves (Alg. 3/6): time, failed rounds,
             and the paper's bound on wasteful steals with measured E and e_s
+  critical_path_trace  per-task trace records of each headline graph read
+            along its critical path: step vs wait per hop, by where each task
+            was taken from
   capturer_baseline  Algorithm 1's CUDA graph of per-task kernels vs the
             persistent scheduler on static DAGs
   composition   module tasks in a loop and parallel joined subflows in one
@@ -38,7 +41,7 @@ Measured in the same run and reported beside it:
             result; each graph is ingested while the previous one runs
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
-                  [--small] [--skip-batched] [--skip-serving] [--skip-extras]
+                  [--small] [--batched-graphs N] [--skip-batched] [--skip-serving] [--skip-extras]
 
 --impl reference times the oracle (the sequential CPU executor) on the
 headline workload, as the comparison arm.  Prints ONE JSON line.
@@ -65,6 +68,7 @@ METRIC = "tasks/s and ns/task overhead, batched vs plain per-graph; serving p50/
 UNIT = "tasks/s"
 WORKLOAD = "large static DAGs, plain form: layered 1000x1000 (d~U{1..8}, R=16) + wavefront 1024x1024 (R=256)"
 SMALL = False   # --small: every section at reduced size (profiler captures; not a bench line)
+BATCHED_GRAPHS = 0   # --batched-graphs: the first N graphs of the batched generator (profiler captures)
 # launch geometries the headline graphs' autotuning picked, for this process only
 TUNE_CACHE = os.path.join(__import__("tempfile").gettempdir(), f"tg_tune_{os.getpid()}.txt")
 
@@ -177,8 +181,8 @@ def run_reference(args):
 # describe the kernel source they were taken on, so they are reported only
 # while tg_kernels.cu still has that hash.
 MEASURED_TRAFFIC = {
-    "kernels_sha256": "08c69df4a019f9d33f8d92d2c10d8e94d840662490e3d4d7ec2dadf8c941a7c2",
-    "bytes_per_launch": {"config2a": 53_150_000, "config2b": 44_490_000},
+    "kernels_sha256": "712b4748bc050e1ee7345eeba054c3d4d22022228bca7156f3993e3f83bd3499",
+    "bytes_per_launch": {"config2a": 52_790_000, "config2b": 44_710_000},
 }
 
 
@@ -496,6 +500,30 @@ def theorem3_bound(run_ns, failed_rounds, round_cycles, workers, E_ns, clock_mhz
             "failed_over_bound": failed_rounds / bound}
 
 
+def critical_path_trace(Executor, B, graphs, tuned):
+    """One run of each headline graph at its tuned geometry with per-task
+    trace records (TG_OPT_TRACE_TASKS: the lean scheduler variant still
+    runs), read along the graph's critical path: how much of each hand-off
+    is the step and how much is waiting, by where the task was taken from."""
+    from paper_2004_10908_b300.trace import critical_path
+    out = {}
+    with Executor(arena_bytes=4 << 30, flags=B.TG_OPT_TRACE_TASKS) as ex:
+        for g in graphs:
+            ex.set_launch(**tuned.get(g.name, {}))
+            h = ex.graph(g)
+            ts = []
+            for _ in range(3):
+                assert ex.run(h) == 0
+                ts.append(ex.stats()["kernel_ns"] / 1e6)
+            st, en, wh = B.tg_trace_copy(ex.ctx, h.handle, g.n)
+            r = critical_path(g.src, g.dst, st, en, wh)
+            r["traced_sched_ms"] = statistics.median(ts)
+            out[g.name] = r
+            h.destroy()
+            ex.set_launch()
+    return out
+
+
 def capturer_baseline(Executor, torch, B):
     """Algorithm 1's form (one kernel per task in a CUDA graph over
     round-robin streams) against the persistent scheduler on static DAGs:
@@ -623,7 +651,10 @@ def B_submit(ex, h):
 def batched(Executor, torch):
     """4,096 graphs in one autotuned, CUDA-graph-captured launch vs one launch each."""
     t0 = time.time()
-    gs = w.config4(n_graphs=256, n_hi=8192) if SMALL else w.config4()
+    if BATCHED_GRAPHS:
+        gs = w.config4(n_graphs=BATCHED_GRAPHS)
+    else:
+        gs = w.config4(n_graphs=256, n_hi=8192) if SMALL else w.config4()
     gen_s = time.time() - t0
     with Executor(arena_bytes=8 << 30, max_nodes=40_000_000, max_edges=450_000_000) as ex:
         hs = [ex.graph(g) for g in gs]
@@ -675,7 +706,8 @@ def batched(Executor, torch):
         plain_s = time.perf_counter() - t1
         b.destroy()
     best_ms = min(ms)
-    return {"workload": "4096 motif graphs, n log-uniform [16, 65536], 5% loop conditions, rounds U{8..512}",
+    n_hi = 8192 if SMALL and not BATCHED_GRAPHS else 65536
+    return {"workload": f"{len(gs)} motif graphs, n log-uniform [16, {n_hi}], 5% loop conditions, rounds U{{8..512}}",
             "graphs": len(gs), "tasks": int(sum(g.n for g in gs)), "executions": int(execs),
             "batched_ms": best_ms, "batched_tasks_s": execs / (best_ms / 1000),
             "plain_s": plain_s, "plain_tasks_s": execs / plain_s,
@@ -1012,6 +1044,7 @@ def run_b300(args):
         section("creation", creation_cost, Executor)
         section("condition_heavy", condition_heavy, Executor, torch, peaks, atom_ceiling)
         section("thief_policies", thief_policies, Executor)
+        section("critical_path_trace", critical_path_trace, Executor, B, graphs, tuned)
         section("capturer_baseline", capturer_baseline, Executor, torch, B)
         section("composition", composition, Executor, torch)
     if rank == 0 and not args.skip_batched:
@@ -1035,13 +1068,17 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="every section small: layered 100x1000 + wavefront 256x256, 256 batched graphs, "
                          "400 served requests (profiler captures; not a bench line)")
+    ap.add_argument("--batched-graphs", type=int, default=0,
+                    help="batched section over the first N graphs of the full-size generator "
+                         "(profiler captures of a mid-size batch; not a bench line)")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-extras", action="store_true",
                     help="leave out the thief-policy and capturer-baseline comparisons")
     args = ap.parse_args()
-    global SMALL
+    global SMALL, BATCHED_GRAPHS
     SMALL = args.small
+    BATCHED_GRAPHS = max(0, args.batched_graphs)
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return

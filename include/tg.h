@@ -103,9 +103,14 @@ enum {
 #define TG_OPT_NO_RACE_CHECK 0x1u   /* skip the per-activation in-flight check (launches whose
                                        graphs have no condition, module or subflow tasks skip it
                                        anyway: every task runs once, a race cannot occur) */
-#define TG_OPT_TRACE 0x2u           /* record per-task start / publish times (tg_trace_copy) and
-                                       per-phase cycle counts, in single-graph and batch launches
-                                       (not in the resident server) */
+#define TG_OPT_TRACE 0x2u           /* TG_OPT_TRACE_TASKS plus per-phase cycle counts
+                                       (tg_ctx_get_stats), which only the extended scheduler
+                                       variant keeps: launches run in it, slower */
+#define TG_OPT_TRACE_TASKS 0x4u     /* record, for every task, when it was taken from a queue,
+                                       when its step ended and where it was taken from
+                                       (tg_trace_copy), in single-graph and batch launches (not
+                                       in the resident server); the launches keep their lean
+                                       scheduler variants and cost about the same */
 
 /* Context options; a zero field selects the default (in brackets). */
 typedef struct {
@@ -438,11 +443,20 @@ int tg_run_noalloc(uint32_t n_nodes, const uint8_t *kinds, const uint32_t *param
                    const uint32_t *succ_off, const uint32_t *succ, uint32_t n_edges, uint32_t seed,
                    uint32_t *out, uint32_t *cnt, uint32_t *dig, void *cuda_stream);
 
-/* With TG_OPT_TRACE: copy the device clock (ns, %globaltimer) at which each
- * task of g last started its payload and last published its successors, for
- * n entries each (start_ns / end_ns may be NULL).  TG_ERR_INVALID without the
- * option. */
-int tg_trace_copy(tg_ctx *ctx, const tg_graph *g, uint64_t *start_ns, uint64_t *end_ns);
+/* Where a traced task was taken from (high half of a tg_trace_copy `where`
+ * word; the low half is the worker block): */
+#define TG_TRACE_FROM_HAND 0u        /* kept by the warp whose step made it ready */
+#define TG_TRACE_FROM_RING 1u        /* the block's shared-memory ring */
+#define TG_TRACE_FROM_OWN_DEQUE 2u   /* the block's own public deque */
+#define TG_TRACE_FROM_STEAL 3u       /* another block's public deque */
+#define TG_TRACE_FROM_INJECTION 4u   /* the shared injection queue (sources) */
+/* With TG_OPT_TRACE_TASKS or TG_OPT_TRACE: for each of g's n tasks, its last
+ * execution's device clock (ns, %globaltimer) when a warp took it from a
+ * queue (start_ns) and when that warp's step ended, before the step's new
+ * activations were published (end_ns), and where it was taken from (where =
+ * TG_TRACE_FROM_* << 16 | worker block).  Any pointer may be NULL.  A task
+ * that never ran reads 0.  TG_ERR_INVALID without either option. */
+int tg_trace_copy(tg_ctx *ctx, const tg_graph *g, uint64_t *start_ns, uint64_t *end_ns, uint32_t *where);
 
 /* The packed form of g as Graphviz DOT text: one node per task ("<id> <kind>
  * R=<rounds>", with the trip or constant of a condition and the composed

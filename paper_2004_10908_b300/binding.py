@@ -20,6 +20,9 @@ TG_ERR_RACE, TG_ERR_EXEC_LIMIT, TG_ERR_TIMEOUT, TG_ERR_CANCELLED = -5, -6, -7, -
 TG_ERR_CUDA, TG_ERR_INTERNAL, TG_ERR_BUSY = -9, -10, -11
 TG_OPT_NO_RACE_CHECK = 0x1
 TG_OPT_TRACE = 0x2
+TG_OPT_TRACE_TASKS = 0x4
+# where a traced task was taken from (tg_trace_copy: where >> 16)
+TG_TRACE_FROM_HAND, TG_TRACE_FROM_RING, TG_TRACE_FROM_OWN_DEQUE, TG_TRACE_FROM_STEAL, TG_TRACE_FROM_INJECTION = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {TG_OK: "OK", TG_PENDING: "PENDING", TG_ERR_INVALID: "INVALID",
                 TG_ERR_NO_SOURCE: "NO_SOURCE", TG_ERR_EDGE_KIND: "EDGE_KIND", TG_ERR_BUDGET: "BUDGET",
@@ -112,7 +115,7 @@ SIGNATURES = {
     "tg_capture_run": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_u64)]),
     "tg_graph_dot": (ctypes.c_int, [_vp, _vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "tg_run_noalloc": (ctypes.c_int, [_u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]),
-    "tg_trace_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "tg_trace_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "tg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -421,8 +424,12 @@ def tg_run_noalloc(n_nodes, kinds_ptr, params_ptr, succ_off_ptr, succ_ptr, n_edg
 
 
 def tg_trace_copy(ctx, g, n):
-    """(start_ns[n], end_ns[n]) of each task's last execution (TG_OPT_TRACE)."""
+    """(start_ns[n], end_ns[n], where[n]) of each task's last execution
+    (TG_OPT_TRACE_TASKS or TG_OPT_TRACE): when a warp took it from a queue,
+    when that step ended, and TG_TRACE_FROM_* << 16 | worker block."""
     a = np.zeros(n, np.uint64)
     b = np.zeros(n, np.uint64)
-    _check(load().tg_trace_copy(_vp(ctx), _vp(g), a.ctypes.data_as(_vp), b.ctypes.data_as(_vp)), "tg_trace_copy")
-    return a, b
+    c = np.zeros(n, np.uint32)
+    _check(load().tg_trace_copy(_vp(ctx), _vp(g), a.ctypes.data_as(_vp), b.ctypes.data_as(_vp),
+                                c.ctypes.data_as(_vp)), "tg_trace_copy")
+    return a, b, c

@@ -183,7 +183,7 @@ struct tg_ctx {
     u32 *outv = nullptr;
     u32 *chunk_gid = nullptr;
     u32 *edges = nullptr;
-    u64 *trace = nullptr;          // TG_OPT_TRACE buffer (2 words per task)
+    u64 *trace = nullptr;          // per-task trace records (3 words per task)
     cudaStream_t side = nullptr;   // instance set-up and server submissions
     SubEntry *sub = nullptr;       // device submission ring
     SubEntry *h_sub = nullptr;     // pinned staging of submission entries
@@ -448,12 +448,13 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
         return TG_ERR_INVALID;
     }
     size_t rest = arena_bytes - off - 4096;
+    const bool traced = (o.flags & (TG_OPT_TRACE | TG_OPT_TRACE_TASKS)) != 0u;
     u64 ncap = o.max_nodes, ecap = o.max_edges;
     ncap &= ~(u64)(kChunk - 1);
     if (ncap == 0) {
         // per task: 36 B execution range + 8 B of injection queue; the edge
         // pool (successor lists and sources) takes the rest
-        ncap = (rest / ((o.flags & TG_OPT_TRACE) ? 144 : 128)) & ~(u64)255;
+        ncap = (rest / (traced ? 152 : 128)) & ~(u64)255;
         if (ncap > kMaxNodeIndex)
             ncap = kMaxNodeIndex & ~(u64)255;
     }
@@ -462,7 +463,7 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
         return TG_ERR_INVALID;
     }
     u64 icap = next_pow2(ncap + 4096);
-    size_t fixed = (size_t)ncap * (sizeof(NodeSlot) + 8 + ((o.flags & TG_OPT_TRACE) ? 16 : 0)) + (size_t)icap * 8 + 4096;
+    size_t fixed = (size_t)ncap * (sizeof(NodeSlot) + 8 + (traced ? 24 : 0)) + (size_t)icap * 8 + 4096;
     if (fixed >= rest) {
         delete c;
         return TG_ERR_INVALID;
@@ -474,8 +475,8 @@ int tg_ctx_create(void *dev_arena, size_t arena_bytes, void *cuda_stream, const 
         return TG_ERR_INVALID;
     }
     c->inj = (u64 *)take((size_t)icap * 8);
-    if (o.flags & TG_OPT_TRACE)
-        c->trace = (u64 *)take((size_t)ncap * 16);
+    if (traced)
+        c->trace = (u64 *)take((size_t)ncap * 24);
     c->slots = (NodeSlot *)take((size_t)ncap * sizeof(NodeSlot));
     c->outv = (u32 *)take((size_t)ncap * 4);
     c->chunk_gid = (u32 *)take((size_t)(ncap >> kChunkShift) * 4 + 256);
@@ -2366,18 +2367,20 @@ extern "C" int tg_serve_replay(tg_ctx *c, tg_graph *const *templates, uint32_t n
 }
 
 
-extern "C" int tg_trace_copy(tg_ctx *c, const tg_graph *g, uint64_t *start_ns, uint64_t *end_ns)
+extern "C" int tg_trace_copy(tg_ctx *c, const tg_graph *g, uint64_t *start_ns, uint64_t *end_ns, uint32_t *where)
 {
     if (!c || !g || g->ctx != c || !c->trace)
         return TG_ERR_INVALID;
     TG_CUDA(cudaStreamSynchronize(c->stream));
-    std::vector<u64> h((size_t)g->n * 2);
-    TG_CUDA(cudaMemcpy(h.data(), c->trace + 2 * g->node_off, h.size() * 8, cudaMemcpyDeviceToHost));
+    std::vector<u64> h((size_t)g->n * 3);
+    TG_CUDA(cudaMemcpy(h.data(), c->trace + 3 * (size_t)g->node_off, h.size() * 8, cudaMemcpyDeviceToHost));
     for (u32 v = 0; v < g->n; ++v) {
         if (start_ns)
-            start_ns[v] = h[2 * (size_t)v];
+            start_ns[v] = h[3 * (size_t)v];
         if (end_ns)
-            end_ns[v] = h[2 * (size_t)v + 1];
+            end_ns[v] = h[3 * (size_t)v + 1];
+        if (where)
+            where[v] = (u32)h[3 * (size_t)v + 2];
     }
     return TG_OK;
 }

@@ -438,7 +438,7 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
 // or subflow tasks, the adaptive thief mode or tracing -- which lives in a
 // separate variant, so that other launches carry none of that code (it costs
 // them 5-19 % per dependency hop, measured).
-template <bool kServe, bool kExt, bool kOne, bool kAcyc = false>
+template <bool kServe, bool kExt, bool kOne, bool kAcyc = false, bool kTrace = false>
 __device__ __forceinline__ void sched_body(const KParams &p)
 {
     extern __shared__ u64 s_ring[];
@@ -543,7 +543,12 @@ __device__ __forceinline__ void sched_body(const KParams &p)
 
     // traced launches: cycles per phase of a step, marked by lane 0 (the
     // previous mark of each warp lives in shared memory)
-    const bool traced = kExt && p.trace != nullptr;
+    const bool traced = kExt && p.trace != nullptr && (p.flags & TG_OPT_TRACE) != 0u;
+    // per-task records (TG_OPT_TRACE_TASKS or TG_OPT_TRACE), compiled only
+    // into the extended and the traced variants: where this warp's current
+    // activations were taken from
+    const bool task_trace = (kExt || kTrace) && !kServe && p.trace != nullptr;
+    u32 from = TG_TRACE_FROM_HAND;
     auto mark = [&](int phase) {
         if (traced && lane == 0) {
             const u64 t = clock64();
@@ -561,10 +566,12 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             k = nh;
             nh = 0;
             st_hand++;
+            from = TG_TRACE_FROM_HAND;
         } else {
             k = ring_pop<true>(w.local, false, lane, e, w.err, bmax);
             if (k) {
                 st_local++;
+                from = TG_TRACE_FROM_RING;
             } else {
                 resume(settle_finish<kServe, kExt>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
                 if (adaptive && busy_w) {
@@ -672,6 +679,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                             emit(w, h, ent, lane, st_spill);
                         }
                         st_inj++;
+                        from = TG_TRACE_FROM_INJECTION;
                         k = ring_pop<true>(w.local, false, lane, e, w.err, bmax);
                     }
                 }
@@ -679,6 +687,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                     k = ring_pop(w.own, false, lane, e, w.err, bmax);
                 if (k) {
                     st_own++;
+                    from = TG_TRACE_FROM_OWN_DEQUE;
                 } else {
                     if (lane == 0 && (vld32(w.avail_word) & w.avail_bit) != 0u) {
                         atomicAnd(w.avail_word, ~w.avail_bit);
@@ -718,6 +727,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                                 k = ring_pop(vr, true, lane, e, w.err, bmax);
                                 if (k) {
                                     st_hit++;
+                                    from = TG_TRACE_FROM_STEAL;
                                 } else if (lane == 0) {
                                     // drained: clear the bit, then re-check so a
                                     // spill that raced with the clear stays visible
@@ -732,6 +742,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                         k = ring_pop(w.inj, true, lane, e, w.err, bmax);
                         if (k)
                             st_inj++;
+                            from = TG_TRACE_FROM_INJECTION;
                     }
                 }
                 if (k == 0) {
@@ -863,6 +874,10 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             u = (u32)e & kIdMask;
             strong = ((u32)e & kStrongBit) != 0u;
             insum = (u32)(e >> 32);
+            if (task_trace) {
+                p.trace[3ull * u] = globaltimer();
+                p.trace[3ull * u + 2ull] = ((u64)from << 16) | (u64)blockIdx.x;
+            }
         }
         uint4 imm = make_uint4(0, 0, 0, 0);
         uint2 stt = make_uint2(0, 0);
@@ -989,8 +1004,6 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         if (act && strong && !acyclic)
             atomicAdd(&p.slots[u].W, (u64)indeg - ((u64)insum << 32));
 
-        if (kExt && p.trace && act)
-            p.trace[2ull * u] = globaltimer();
         // ---- payload
         const u32 x = cont ? __ldcg(&p.outv[u]) +
                                  (kind == TG_SUBFLOW ? vld32(&p.descs[ld_imm<kServe>(&p.edges[imm.x])].acc) : 0u)
@@ -1281,8 +1294,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 }
             }
         }
-        if (kExt && p.trace && act)
-            p.trace[2ull * u + 1ull] = globaltimer();
+        if (task_trace && act)
+            p.trace[3ull * u + 1ull] = globaltimer();
         // ---- a warp whose step produced at most kHandMax activations runs
         // them itself next (a chain never leaves the warp); wider output is
         // published to the block's ring / public deque, where it merges with
@@ -1390,12 +1403,22 @@ __device__ __forceinline__ void sched_body(const KParams &p)
 
 // One-shot launches (single graphs, batches): at most 512 threads (16 worker
 // warps), so that 128 registers per thread fill the SM.  kOne: one graph;
-// kAcyc: one graph without condition tasks (every task static, run once).
-template <bool kExt, bool kOne, bool kAcyc = false>
+// kAcyc: one graph without condition tasks (every task static, run once);
+// kTrace: records per-task trace words (TG_OPT_TRACE_TASKS), a copy of the
+// lean variant so that untraced launches carry none of it.
+template <bool kExt, bool kOne, bool kAcyc = false, bool kTrace = false>
 __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
 {
-    sched_body<false, kExt, kOne, kAcyc>(p);
+    sched_body<false, kExt, kOne, kAcyc, kTrace>(p);
 }
+
+// every one-shot variant: they share the block shape a geometry allows
+using SchedFn = void (*)(KParams);
+const SchedFn kOneShotVariants[] = {
+    sched_kernel<true, false>,        sched_kernel<false, true>,        sched_kernel<false, true, true>,
+    sched_kernel<false, false>,       sched_kernel<false, true, false, true>, sched_kernel<false, true, true, true>,
+    sched_kernel<false, false, false, true>,
+};
 
 // The resident server (its blocks are at most half an SM).
 __global__ void serve_kernel(KParams p)
@@ -1422,6 +1445,11 @@ __global__ void rearm_kernel(KParams p)
         p.slots[u].W = (u64)(deg >> 16);
         *reinterpret_cast<uint2 *>(&p.slots[u].cnt) = make_uint2(0u, 0u);
         p.outv[u] = 0u;
+        if (p.trace) {
+            p.trace[3ull * u] = 0ull;
+            p.trace[3ull * u + 1ull] = 0ull;
+            p.trace[3ull * u + 2ull] = 0ull;
+        }
     }
     // the successor lists of this block's tasks are pulled into L2 ahead of
     // the scheduler, which reads each once, on its critical path
@@ -1647,18 +1675,11 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dyn_smem > raised[dev]) {
-            e = cudaFuncSetAttribute(sched_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-            if (e != cudaSuccess)
-                return e;
-            e = cudaFuncSetAttribute(sched_kernel<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-            if (e != cudaSuccess)
-                return e;
-            e = cudaFuncSetAttribute(sched_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-            if (e != cudaSuccess)
-                return e;
-            e = cudaFuncSetAttribute(sched_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-            if (e != cudaSuccess)
-                return e;
+            for (SchedFn f : kOneShotVariants) {
+                e = cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+                if (e != cudaSuccess)
+                    return e;
+            }
             e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess)
                 return e;
@@ -1667,21 +1688,17 @@ cudaError_t sched_occupancy(int threads, size_t dyn_smem, int *blocks_per_sm, bo
     }
     if (serve)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, serve_kernel, threads, dyn_smem);
-    // the extended variant must fit the same block shape
-    int ext = 0, one = 0, acyc = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ext, sched_kernel<true, false>, threads, dyn_smem);
-    if (e != cudaSuccess)
-        return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&one, sched_kernel<false, true>, threads, dyn_smem);
-    if (e != cudaSuccess)
-        return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&acyc, sched_kernel<false, true, true>, threads, dyn_smem);
-    if (e != cudaSuccess)
-        return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sched_kernel<false, false>, threads, dyn_smem);
-    if (e == cudaSuccess)
-        *blocks_per_sm = std::min(*blocks_per_sm, std::min(ext, std::min(one, acyc)));
-    return e;
+    // every variant must fit the same block shape
+    int fewest = 1 << 30;
+    for (SchedFn f : kOneShotVariants) {
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void *)f, threads, dyn_smem);
+        if (e != cudaSuccess)
+            return e;
+        fewest = std::min(fewest, b);
+    }
+    *blocks_per_sm = fewest;
+    return cudaSuccess;
 }
 
 cudaError_t launch_rearm(const KParams &p, cudaStream_t st)
@@ -1706,8 +1723,14 @@ cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t
     if (serve)
         serve_kernel<<<blocks, threads, smem, st>>>(p);
     else
-        if (p.has_modules || p.thief_mode == 1u || p.trace != nullptr)
+        if (p.has_modules || p.thief_mode == 1u || (p.flags & TG_OPT_TRACE) != 0u)
             sched_kernel<true, false><<<blocks, threads, smem, st>>>(p);
+        else if (p.trace != nullptr && p.lt == nullptr && (p.flags & kFlagAcyclic) != 0u)
+            sched_kernel<false, true, true, true><<<blocks, threads, smem, st>>>(p);
+        else if (p.trace != nullptr && p.lt == nullptr)
+            sched_kernel<false, true, false, true><<<blocks, threads, smem, st>>>(p);
+        else if (p.trace != nullptr)
+            sched_kernel<false, false, false, true><<<blocks, threads, smem, st>>>(p);
         else if (p.lt == nullptr && (p.flags & kFlagAcyclic) != 0u)
             sched_kernel<false, true, true><<<blocks, threads, smem, st>>>(p);
         else if (p.lt == nullptr)

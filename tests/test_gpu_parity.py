@@ -306,10 +306,44 @@ def test_tracing_keeps_results_and_records_times():
         assert_same((st,) + tuple(e.result(gh)), ref, "traced")
         s = e.stats()
         assert all(c > 0 for c in s["phase_cycles"])
-        t0, t1 = B.tg_trace_copy(e.ctx, gh.handle, g.n)
+        t0, t1, wh = B.tg_trace_copy(e.ctx, gh.handle, g.n)
         ran = ref.cnt > 0
         assert (t0[ran] > 0).all() and (t1[ran] >= t0[ran]).all()
+        assert ((wh[ran] >> 16) <= B.TG_TRACE_FROM_INJECTION).all()
         gh.destroy()
+
+
+def test_task_trace_in_the_lean_variant_reads_the_critical_path():
+    """TG_OPT_TRACE_TASKS keeps the lean scheduler variant: results equal the
+    oracle, every task carries a take time, a later step end and where it
+    came from, the sources came from the injection queue, and on a layered
+    DAG (every task has a predecessor one level up) the chain of
+    last-finishing predecessors crosses every level exactly once."""
+    from paper_2004_10908_b300 import Executor, binding as B
+    from paper_2004_10908_b300.trace import critical_path
+    levels, width = 40, 300
+    g = w.config2a(seed=5, levels=levels, width=width, d_lo=1, d_hi=6, rounds=8)
+    ref = oracle.run(g)
+    with Executor(arena_bytes=1 << 28, flags=B.TG_OPT_TRACE_TASKS) as e:
+        for geo in (dict(), dict(warps_per_block=4, worker_blocks=296, batch_max=8)):
+            e.set_launch(**geo)
+            gh = e.graph(g)
+            st = e.run(gh)
+            assert_same((st,) + tuple(e.result(gh)), ref, f"task trace {geo}")
+            assert all(c == 0 for c in e.stats()["phase_cycles"])   # no phase counters: lean variant
+            t0, t1, wh = B.tg_trace_copy(e.ctx, gh.handle, g.n)
+            assert (t0 > 0).all() and (t1 >= t0).all()
+            frm = wh >> 16
+            assert (frm <= B.TG_TRACE_FROM_INJECTION).all()
+            assert ((wh & 0xFFFF) < e.stats()["worker_blocks"]).all()
+            assert (frm[:width] == B.TG_TRACE_FROM_INJECTION).all()   # level 0: the sources
+            cp = critical_path(g.src, g.dst, t0, t1, wh)
+            last_level = int(np.argmax(t1)) // width
+            assert cp["tasks"] == last_level + 1 and last_level >= levels - 2
+            assert sum(v["hops"] for v in cp["hops_by_source"].values()) == last_level
+            assert sum(cp["all_tasks_by_source"].values()) == g.n
+            gh.destroy()
+        e.set_launch()
 
 
 def test_looping_graphs_never_report_a_false_race():
