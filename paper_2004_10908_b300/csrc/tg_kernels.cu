@@ -440,7 +440,45 @@ __device__ __forceinline__ void stage(WarpCtx &w, u64 *buf, u32 &ns, bool has, u
 __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, u32 &spill_ctr, u64 *pe_order = nullptr)
 {
     __syncwarp();
-    for (u32 i = 0; i < ns; i += 32u) {
+    u32 done = 0;
+    if (ns > 32u) {
+        // one reservation of the block ring's slots for the batches that the
+        // per-batch rule in emit would keep local (a batch of 32 stays in the
+        // block while the ring holds fewer than the backlog limit), instead of
+        // one reservation per batch of 32 after the previous batch's
+        u32 t = 0, nl = 0;
+        if (lane == 0) {
+            for (int tr = 0; tr < kCasTries; ++tr) {
+                const u32 tt = lds32(w.local.tail), hh = lds32(w.local.head);
+                const u32 lsz = tt - hh;
+                const u32 thr = (i32)w.hungry_v > 0 ? w.high_water : w.keep_hi;
+                u32 want = lsz < thr ? min(ns, ((thr - lsz + 31u) / 32u) * 32u) : 0u;
+                want = min(want, (w.local.mask + 1u) - min(lsz, w.local.mask + 1u));
+                if (want == 0u)
+                    break;
+                if (cas_s32(w.local.tail, tt, tt + want) == tt) {
+                    t = tt;
+                    nl = want;
+                    break;
+                }
+            }
+        }
+        nl = __shfl_sync(kFull, nl, 0);
+        t = __shfl_sync(kFull, t, 0);
+        for (u32 j = (u32)lane; j < nl; j += 32u) {
+            u64 *slot = w.local.slots + ((t + j) & w.local.mask);
+            int spins = 0;
+            while ((u32)lds64(slot) != kEmpty32) {   // previous occupant not yet taken
+                if (++spins > kSpinLimit) {
+                    w.err = 1;
+                    break;
+                }
+            }
+            sts64(slot, buf[j]);
+        }
+        done = nl;
+    }
+    for (u32 i = done; i < ns; i += 32u) {
         const bool h = i + (u32)lane < ns;
         emit(w, h, h ? buf[i + lane] : 0ull, lane, spill_ctr, pe_order);
     }
