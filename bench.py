@@ -372,7 +372,8 @@ def plain_single_graph(Executor, torch, B):
             "empty_launch_sync_us": statistics.median(empty[3:]),
             "dependency_floor_us": floor_ns / 1e3, "critical_path_tasks": 61,
             "floor_frac": floor_ns / 1e3 / k,
-            "launch_geometry": {kk: chosen[kk] for kk in ("worker_blocks", "warps_per_block", "batch_max", "thief_mode")},
+            "launch_geometry": {kk: chosen[kk] for kk in ("worker_blocks", "warps_per_block", "batch_max", "local_keep",
+                                                         "keep_idle", "thief_mode")},
             "oracle_match": ok, "oracle_1core_us": oracle_s * 1e6}
 
 

@@ -141,6 +141,12 @@ typedef struct {
                                   find spilled work sooner on wide graphs; long ones leave
                                   the memory system to the busy warps of a long chain
                                   (at most 1,000,000) [512] */
+    int32_t keep_idle;         /* 1: while another block is hungry, a block keeps beyond
+                                  local_keep as many ready activations as its idle warps can
+                                  take at once, before any goes to its stealable deque;
+                                  0: it keeps local_keep.  Read by single-graph launches of
+                                  graphs with condition tasks (a compiled variant of its
+                                  own); other launches ignore it [0] */
 } tg_ctx_opts;
 
 /* Create a context on the current CUDA device.
@@ -304,8 +310,8 @@ int tg_batch_wait(tg_ctx *ctx, tg_batch *b, int *statuses);
 int tg_batch_destroy(tg_ctx *ctx, tg_batch *b);
 /* Autotune a batch (worker-block count, warps per block, deque depth, steal
  * policy, victims per steal round, thief slots, activations per warp step,
- * local backlog, thief mode, a thief's longest sleep and an idle warp's
- * sleep): time its launch under
+ * local backlog and whether idle warps extend it, thief mode, a thief's
+ * longest sleep and an idle warp's sleep): time its launch under
  * candidate geometries by coordinate descent, `trials` timed launches each,
  * keep the fastest and re-capture the batch with it.  With cache_path
  * non-NULL, a result cached for the same device and batch shape (graph,
@@ -363,8 +369,8 @@ int tg_ctx_get_opts(const tg_ctx *ctx, tg_ctx_opts *opts);
 /* Change the launch geometry used by later single-graph launches and by
  * batches created afterwards.  Reads worker_blocks, warps_per_block,
  * deque_depth (at most the context's), steal_policy, max_steal, smem_ring,
- * idle_sleep_ns, max_thieves, batch_max, local_keep, thief_mode and
- * steal_backoff_ns (0 = default); other fields are ignored.
+ * idle_sleep_ns, max_thieves, batch_max, local_keep, thief_mode,
+ * steal_backoff_ns and keep_idle (0 = default); other fields are ignored.
  * TG_ERR_INVALID if a field is out of range or the block shape cannot be
  * resident. */
 int tg_ctx_set_launch(tg_ctx *ctx, const tg_ctx_opts *launch);

@@ -277,6 +277,9 @@ struct WarpCtx {
     Ring inj;        // shared injection queue
     u32 high_water;  // local ring size above which new work goes public while a block is hungry
     u32 keep_hi;     // local ring size above which new work always goes public
+    const u32 *busy; // keep_idle launches: the block's warps executing work (shared memory)
+    u32 nwarps;      // the block's warps
+    u32 bmax;        // activations a warp takes per step
     const u32 *hungry;  // blocks whose thief found no work anywhere
     u32 hungry_v;       // lane 0: its value, loaded at the start of the warp's step
     u32 *avail_word; // this block's word / bit in the work-available bitmap
@@ -284,7 +287,22 @@ struct WarpCtx {
     int err;
 };
 
+// The backlog a block keeps while another block is hungry: local_keep, and
+// with keep_idle as much as its idle warps can take at once (a backlog that
+// they start at once would only wait for a thief in a public deque).  kIdle:
+// compiled in, in a variant of its own (the extra code alone cost the other
+// variants 2-6 % per hop).
+template <bool kIdle>
+__device__ __forceinline__ u32 local_limit(const WarpCtx &w)
+{
+    if (!kIdle || !w.busy)
+        return w.high_water;
+    const u32 idle = w.nwarps - min(lds32(w.busy), w.nwarps);
+    return max(w.high_water, idle * w.bmax);
+}
+
 // Route the new ready activations of the warp (lanes with `has`).
+template <bool kIdle = false>
 __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u32 &spill_ctr, u64 *pe_order = nullptr)
 {
     if (__ballot_sync(kFull, has) == 0)
@@ -295,7 +313,7 @@ __device__ __forceinline__ void emit(WarpCtx &w, bool has, u64 ent, int lane, u3
     int spill = 0;
     if (lane == 0) {
         const u32 lsz = ring_size<true>(w.local);
-        spill = lsz >= w.keep_hi || (lsz >= w.high_water && (i32)w.hungry_v > 0);
+        spill = lsz >= w.keep_hi || (lsz >= local_limit<kIdle>(w) && (i32)w.hungry_v > 0);
     }
     spill = __shfl_sync(kFull, spill, 0);
     bool pub = has && spill;
@@ -437,6 +455,7 @@ __device__ __forceinline__ void stage(WarpCtx &w, u64 *buf, u32 &ns, bool has, u
     ns += k;
 }
 
+template <bool kIdle = false>
 __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, u32 &spill_ctr, u64 *pe_order = nullptr)
 {
     __syncwarp();
@@ -451,7 +470,7 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
             for (int tr = 0; tr < kCasTries; ++tr) {
                 const u32 tt = lds32(w.local.tail), hh = lds32(w.local.head);
                 const u32 lsz = tt - hh;
-                const u32 thr = (i32)w.hungry_v > 0 ? w.high_water : w.keep_hi;
+                const u32 thr = (i32)w.hungry_v > 0 ? min(local_limit<kIdle>(w), w.keep_hi) : w.keep_hi;
                 u32 want = lsz < thr ? min(ns, ((thr - lsz + 31u) / 32u) * 32u) : 0u;
                 want = min(want, (w.local.mask + 1u) - min(lsz, w.local.mask + 1u));
                 if (want == 0u)
@@ -480,7 +499,7 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
     }
     for (u32 i = done; i < ns; i += 32u) {
         const bool h = i + (u32)lane < ns;
-        emit(w, h, h ? buf[i + lane] : 0ull, lane, spill_ctr, pe_order);
+        emit<kIdle>(w, h, h ? buf[i + lane] : 0ull, lane, spill_ctr, pe_order);
     }
 }
 
@@ -488,7 +507,7 @@ __device__ __forceinline__ void publish(WarpCtx &w, u64 *buf, u32 ns, int lane, 
 // or subflow tasks, the adaptive thief mode or tracing -- which lives in a
 // separate variant, so that other launches carry none of that code (it costs
 // them 5-19 % per dependency hop, measured).
-template <bool kServe, bool kExt, bool kOne, bool kAcyc = false, bool kTrace = false>
+template <bool kServe, bool kExt, bool kOne, bool kAcyc = false, bool kTrace = false, bool kIdle = false>
 __device__ __forceinline__ void sched_body(const KParams &p)
 {
     extern __shared__ u64 s_ring[];
@@ -525,6 +544,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     // fence of its own.
     // (kAcyc: the same known at compile time, every task is a static one)
     const bool acyclic = kAcyc || (!kServe && (p.flags & kFlagAcyclic) != 0u);
+
     const bool race_check = !acyclic && (p.flags & TG_OPT_NO_RACE_CHECK) == 0;
     const int bmax = (int)min(32u, max(1u, p.batch_max));
     // one graph: every activation has gid == single_gid (not when it composes others)
@@ -546,6 +566,9 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     // them), half the ring while none is
     w.high_water = min(p.local_keep ? p.local_keep : 32u, ring_n);
     w.keep_hi = max(w.high_water, ring_n / 2u);
+    w.busy = (kIdle && p.keep_idle) ? &s_busy : nullptr;
+    w.nwarps = blockDim.x >> 5;
+    w.bmax = (u32)bmax;
     w.hungry = &p.ctl->hungry;
     w.hungry_v = 0;
     w.err = 0;
@@ -573,6 +596,8 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     // adaptive thieves (Alg. 3/6 invariant): a block is active while one of
     // its warps executes; blocks are the workers whose counts are kept
     const bool adaptive = !kServe && kExt && p.thief_mode == 1u;
+    // busy warps are counted for the adaptive thieves and for keep_idle
+    const bool count_busy = adaptive || (kIdle && p.keep_idle != 0u);
     bool busy_w = false;
     u32 rng = mix32(blockIdx.x * 0x9E3779B9U + (u32)warp * 0x85EBCA6BU + 1u);
     bool pend = false;      // a pending-count update whose result is not examined yet
@@ -624,9 +649,9 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 from = TG_TRACE_FROM_RING;
             } else {
                 resume(settle_finish<kServe, kExt>(p, pend, pend_old, pend_delta, pend_g, pend_cap), st_spill);
-                if (adaptive && busy_w) {
+                if (count_busy && busy_w) {
                     busy_w = false;
-                    if (lane == 0 && atomicSub(&s_busy, 1u) == 1u)
+                    if (lane == 0 && atomicSub(&s_busy, 1u) == 1u && adaptive)
                         atomicSub(&p.ctl->actives, 1u);
                 }
                 // ---- idle.  One warp per block at a time is the block's thief
@@ -902,9 +927,9 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         }
         st_iters++;
         mark(0);
-        if (adaptive && !busy_w) {
+        if (count_busy && !busy_w) {
             busy_w = true;
-            if (lane == 0 && atomicAdd(&s_busy, 1u) == 0u)
+            if (lane == 0 && atomicAdd(&s_busy, 1u) == 0u && adaptive)
                 atomicAdd(&p.ctl->actives, 1u);
         }
         if (lane == 0 && *(volatile int *)&s_hungry != 0 && atomicExch(&s_hungry, 0) == 1)
@@ -1356,7 +1381,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             hand = (u32)lane < keep ? my_stage[lane] : kEmpty;
             nh = (int)keep;
             if (ns > keep)
-                publish(w, my_stage + keep, ns - keep, lane, st_spill, kAcyc ? &p.descs[p.single_gid].pe : nullptr);
+                publish<kIdle>(w, my_stage + keep, ns - keep, lane, st_spill, kAcyc ? &p.descs[p.single_gid].pe : nullptr);
             __syncwarp();
         }
 
@@ -1455,11 +1480,12 @@ __device__ __forceinline__ void sched_body(const KParams &p)
 // warps), so that 128 registers per thread fill the SM.  kOne: one graph;
 // kAcyc: one graph without condition tasks (every task static, run once);
 // kTrace: records per-task trace words (TG_OPT_TRACE_TASKS), a copy of the
-// lean variant so that untraced launches carry none of it.
-template <bool kExt, bool kOne, bool kAcyc = false, bool kTrace = false>
+// lean variant so that untraced launches carry none of it; kIdle: keep_idle
+// (one graph with condition tasks).
+template <bool kExt, bool kOne, bool kAcyc = false, bool kTrace = false, bool kIdle = false>
 __global__ void __launch_bounds__(512, 1) sched_kernel(KParams p)
 {
-    sched_body<false, kExt, kOne, kAcyc, kTrace>(p);
+    sched_body<false, kExt, kOne, kAcyc, kTrace, kIdle>(p);
 }
 
 // every one-shot variant: they share the block shape a geometry allows
@@ -1467,7 +1493,7 @@ using SchedFn = void (*)(KParams);
 const SchedFn kOneShotVariants[] = {
     sched_kernel<true, false>,        sched_kernel<false, true>,        sched_kernel<false, true, true>,
     sched_kernel<false, false>,       sched_kernel<false, true, false, true>, sched_kernel<false, true, true, true>,
-    sched_kernel<false, false, false, true>,
+    sched_kernel<false, false, false, true>, sched_kernel<false, true, false, false, true>,
 };
 
 // The resident server (its blocks are at most half an SM).
@@ -1783,6 +1809,8 @@ cudaError_t launch_sched(const KParams &p, int blocks, int threads, cudaStream_t
             sched_kernel<false, false, false, true><<<blocks, threads, smem, st>>>(p);
         else if (p.lt == nullptr && (p.flags & kFlagAcyclic) != 0u)
             sched_kernel<false, true, true><<<blocks, threads, smem, st>>>(p);
+        else if (p.lt == nullptr && p.keep_idle != 0u)
+            sched_kernel<false, true, false, false, true><<<blocks, threads, smem, st>>>(p);
         else if (p.lt == nullptr)
             sched_kernel<false, true><<<blocks, threads, smem, st>>>(p);
         else

@@ -52,8 +52,9 @@ class Executor:
     arena_bytes: size of the torch-allocated device arena the library
     sub-allocates; stream: a torch.cuda.Stream (default: a new one);
     opts: any tg_ctx_opts field (worker_blocks, warps_per_block, deque_depth,
-    steal_policy, max_steal, smem_ring, flags, time_limit_ns, exec_cap,
-    mem_budget_bytes, max_nodes, max_edges)."""
+    steal_policy, max_steal, smem_ring, flags, idle_sleep_ns, max_thieves,
+    batch_max, local_keep, thief_mode, time_limit_ns, exec_cap,
+    mem_budget_bytes, max_nodes, max_edges, steal_backoff_ns, keep_idle)."""
 
     def __init__(self, arena_bytes: int = 1 << 30, stream=None, **opts):
         import torch

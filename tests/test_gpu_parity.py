@@ -357,7 +357,8 @@ def test_looping_graphs_never_report_a_false_race():
               w.config3(seed=4, n_cond=80, body_levels=3, body_width=5, rounds=4, trip_max=6)] + \
              [w.nested_loops(s) for s in range(3)]
     refs = [oracle.run(g) for g in graphs]
-    for geo in (dict(), dict(warps_per_block=4, worker_blocks=592), dict(warps_per_block=8, batch_max=8)):
+    for geo in (dict(), dict(warps_per_block=4, worker_blocks=592), dict(warps_per_block=8, batch_max=8),
+                dict(keep_idle=1), dict(keep_idle=1, warps_per_block=4, worker_blocks=296, local_keep=16)):
         with Executor(arena_bytes=1 << 29, **geo) as ex:
             hs = [ex.graph(g) for g in graphs]
             for _ in range(8):
