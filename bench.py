@@ -716,6 +716,7 @@ def batched(Executor, torch):
             "ns_per_task_overhead": (best_ms * 1e6 - pay_ns) / execs,
             "payload_only_ms": pay_ns / 1e6, "payload_only_frac": (pay_ns / 1e6) / best_ms,
             "payload_only_task_order_ms": pay_task / 1e6,
+            "payload_only_task_order_frac": (pay_task / 1e6) / best_ms,
             "payload_ceiling": "the executed (id, iter, rounds) multiset, one thread per task, sorted by work",
             "mean_rounds": rounds / execs,
             "oracle_checked_graphs": checked, "oracle_match": ok,
