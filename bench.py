@@ -224,7 +224,7 @@ def headline(ex, graphs, args, torch, B, world=1):
         chosen, _ = ex.autotune(h, trials=2, cache_path=TUNE_CACHE)
         tuned[g.name] = {k: chosen[k] for k in ("worker_blocks", "warps_per_block", "batch_max", "local_keep",
                                                 "max_thieves", "thief_mode", "steal_policy", "max_steal",
-                                                "steal_backoff_ns", "idle_sleep_ns")}
+                                                "steal_backoff_ns", "idle_sleep_ns", "hand_batch")}
     tuned["autotune_s"] = time.perf_counter() - t0
 
     def step():
@@ -373,7 +373,7 @@ def plain_single_graph(Executor, torch, B):
             "dependency_floor_us": floor_ns / 1e3, "critical_path_tasks": 61,
             "floor_frac": floor_ns / 1e3 / k,
             "launch_geometry": {kk: chosen[kk] for kk in ("worker_blocks", "warps_per_block", "batch_max", "local_keep",
-                                                         "keep_idle", "thief_mode")},
+                                                         "keep_idle", "hand_batch", "thief_mode")},
             "oracle_match": ok, "oracle_1core_us": oracle_s * 1e6}
 
 
@@ -722,7 +722,7 @@ def batched(Executor, torch):
             "oracle_checked_graphs": checked, "oracle_match": ok,
             "autotuned": {k: chosen[k] for k in ("worker_blocks", "warps_per_block", "deque_depth",
                                                  "steal_policy", "max_steal", "max_thieves", "batch_max",
-                                                 "local_keep", "steal_backoff_ns", "idle_sleep_ns")},
+                                                 "local_keep", "steal_backoff_ns", "idle_sleep_ns", "hand_batch")},
             "autotune_s": tune_s, "generate_s": gen_s,
             "cpu_all_cores": oracle_all_cores(gs[::8], "every 8th graph of the batch")}
 

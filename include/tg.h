@@ -147,6 +147,10 @@ typedef struct {
                                   0: it keeps local_keep.  Read by single-graph launches of
                                   graphs with condition tasks (a compiled variant of its
                                   own); other launches ignore it [0] */
+    int32_t hand_batch;        /* 1: a warp whose step made at most batch_max activations
+                                  ready keeps them all for its own next step while its
+                                  block's ring is empty; 0: it keeps at most 2 and publishes
+                                  the rest [0] */
 } tg_ctx_opts;
 
 /* Create a context on the current CUDA device.
@@ -310,8 +314,9 @@ int tg_batch_wait(tg_ctx *ctx, tg_batch *b, int *statuses);
 int tg_batch_destroy(tg_ctx *ctx, tg_batch *b);
 /* Autotune a batch (worker-block count, warps per block, deque depth, steal
  * policy, victims per steal round, thief slots, activations per warp step,
- * local backlog and whether idle warps extend it, thief mode, a thief's
- * longest sleep and an idle warp's sleep): time its launch under
+ * local backlog and whether idle warps extend it, how much of a step's
+ * output its warp keeps, thief mode, a thief's longest sleep and an idle
+ * warp's sleep): time its launch under
  * candidate geometries by coordinate descent, `trials` timed launches each,
  * keep the fastest and re-capture the batch with it.  With cache_path
  * non-NULL, a result cached for the same device and batch shape (graph,
@@ -370,7 +375,8 @@ int tg_ctx_get_opts(const tg_ctx *ctx, tg_ctx_opts *opts);
  * batches created afterwards.  Reads worker_blocks, warps_per_block,
  * deque_depth (at most the context's), steal_policy, max_steal, smem_ring,
  * idle_sleep_ns, max_thieves, batch_max, local_keep, thief_mode,
- * steal_backoff_ns and keep_idle (0 = default); other fields are ignored.
+ * steal_backoff_ns, keep_idle and hand_batch (0 = default); other fields are
+ * ignored.
  * TG_ERR_INVALID if a field is out of range or the block shape cannot be
  * resident. */
 int tg_ctx_set_launch(tg_ctx *ctx, const tg_ctx_opts *launch);

@@ -46,7 +46,8 @@ class tg_ctx_opts(ctypes.Structure):
                 ("local_keep", ctypes.c_int32), ("thief_mode", ctypes.c_int32),
                 ("time_limit_ns", ctypes.c_uint64), ("exec_cap", ctypes.c_uint64),
                 ("mem_budget_bytes", ctypes.c_uint64), ("max_nodes", ctypes.c_uint64),
-                ("max_edges", ctypes.c_uint64), ("steal_backoff_ns", ctypes.c_uint32), ("keep_idle", ctypes.c_int32)]
+                ("max_edges", ctypes.c_uint64), ("steal_backoff_ns", ctypes.c_uint32), ("keep_idle", ctypes.c_int32),
+                ("hand_batch", ctypes.c_int32)]
 
 
 class tg_graph_info(ctypes.Structure):

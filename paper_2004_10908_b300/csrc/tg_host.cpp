@@ -34,7 +34,7 @@ constexpr u32 kSubRing = 1u << 16;  // server-mode submission / completion ring 
 struct Geometry {
     int blocks = 0, threads = 0;
     u32 ring = 0, depth = 0, policy = 0, max_steal = 0, thieves = 0, idle_ns = 0, batch = 32, keep = 0, tmode = 0,
-        backoff = 512, keep_idle = 0;
+        backoff = 512, keep_idle = 0, hand_batch = 0;
 };
 
 u64 now_ns()
@@ -255,6 +255,7 @@ KParams base_params(tg_ctx *c, const Geometry &g)
     p.thief_mode = g.tmode;
     p.steal_backoff_ns = g.backoff;
     p.keep_idle = g.keep_idle;
+    p.hand_batch = g.hand_batch;
     p.thief_slots = c->thief_slots;
     p.time_limit_ns = c->opts.time_limit_ns;
     p.cancel = c->d_cancel;
@@ -323,7 +324,7 @@ int resolve_geometry(const tg_ctx *c, const tg_ctx_opts &o, Geometry &g)
         depth > c->dq_cap || o.steal_policy < 0 || o.steal_policy > 1 || o.max_thieves > 1024 ||
         o.max_steal < 0 || o.worker_blocks < 0 || o.batch_max < 0 || o.batch_max > 32 || o.local_keep < 0 ||
         (u32)o.local_keep > ring || o.thief_mode < 0 || o.thief_mode > 1 || o.steal_backoff_ns > 1000000u ||
-        o.keep_idle < 0 || o.keep_idle > 1)
+        o.keep_idle < 0 || o.keep_idle > 1 || o.hand_batch < 0 || o.hand_batch > 1)
         return TG_ERR_INVALID;
     int per_sm = 0;
     if (sched_occupancy(warps * 32, sched_dyn_smem(ring, (u32)warps), &per_sm) != cudaSuccess || per_sm <= 0)
@@ -344,6 +345,7 @@ int resolve_geometry(const tg_ctx *c, const tg_ctx_opts &o, Geometry &g)
     g.tmode = (u32)o.thief_mode;
     g.backoff = o.steal_backoff_ns > 0 ? o.steal_backoff_ns : 512u;
     g.keep_idle = (u32)o.keep_idle;
+    g.hand_batch = (u32)o.hand_batch;
     return TG_OK;
 }
 
@@ -362,6 +364,7 @@ void geometry_to_opts(const Geometry &g, tg_ctx_opts &o)
     o.thief_mode = (int32_t)g.tmode;
     o.steal_backoff_ns = g.backoff;
     o.keep_idle = (int32_t)g.keep_idle;
+    o.hand_batch = (int32_t)g.hand_batch;
 }
 
 }  // namespace
@@ -1758,10 +1761,10 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
                     continue;
                 tg_ctx_opts o{};
                 unsigned long long t = 0;
-                if (std::sscanf(tab + 1, "%d %d %d %d %d %d %d %u %d %d %d %u %d %llu", &o.worker_blocks,
+                if (std::sscanf(tab + 1, "%d %d %d %d %d %d %d %u %d %d %d %u %d %d %llu", &o.worker_blocks,
                                 &o.warps_per_block, &o.deque_depth, &o.steal_policy, &o.max_steal, &o.max_thieves,
                                 &o.smem_ring, &o.idle_sleep_ns, &o.batch_max, &o.local_keep, &o.thief_mode,
-                                &o.steal_backoff_ns, &o.keep_idle, &t) == 14) {
+                                &o.steal_backoff_ns, &o.keep_idle, &o.hand_batch, &t) == 15) {
                     Geometry g;
                     if (resolve_geometry(c, o, g) == TG_OK) {
                         best = o;
@@ -1790,6 +1793,7 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
     const int backoff_c[] = {512, 4096};
     const int idle_c[] = {256, 1024};
     const int keep_idle_c[] = {0, 1};
+    const int hand_batch_c[] = {0, 1};
     auto try_knob = [&](auto setter, const int *vals, int nv) -> int {
         for (int i = 0; i < nv; ++i) {
             tg_ctx_opts o = best;
@@ -1826,6 +1830,7 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
             (rc = try_knob([](tg_ctx_opts &o, int v) { o.batch_max = v; }, batch_c, 4)) != TG_OK ||
             (rc = try_knob([](tg_ctx_opts &o, int v) { o.local_keep = v; }, keep_c, 5)) != TG_OK ||
             (rc = try_knob([](tg_ctx_opts &o, int v) { o.keep_idle = v; }, keep_idle_c, 2)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.hand_batch = v; }, hand_batch_c, 2)) != TG_OK ||
             (rc = try_knob([](tg_ctx_opts &o, int v) { o.thief_mode = v; }, tmode_c, 2)) != TG_OK ||
             (rc = try_knob([](tg_ctx_opts &o, int v) { o.steal_backoff_ns = (u32)v; }, backoff_c, 2)) != TG_OK ||
             (rc = try_knob([](tg_ctx_opts &o, int v) { o.idle_sleep_ns = (u32)v; }, idle_c, 2)) != TG_OK)
@@ -1835,10 +1840,11 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
     }
     if (cache_path) {
         if (FILE *f = std::fopen(cache_path, "a")) {
-            std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %d %d %d %u %d %llu\n", key.c_str(), best.worker_blocks,
+            std::fprintf(f, "%s\t%d %d %d %d %d %d %d %u %d %d %d %u %d %d %llu\n", key.c_str(), best.worker_blocks,
                          best.warps_per_block, best.deque_depth, best.steal_policy, best.max_steal,
                          best.max_thieves, best.smem_ring, best.idle_sleep_ns, best.batch_max, best.local_keep,
-                         best.thief_mode, best.steal_backoff_ns, best.keep_idle, (unsigned long long)best_t);
+                         best.thief_mode, best.steal_backoff_ns, best.keep_idle, best.hand_batch,
+                         (unsigned long long)best_t);
             std::fclose(f);
         }
     }

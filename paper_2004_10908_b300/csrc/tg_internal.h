@@ -150,7 +150,7 @@ struct KParams {
     u32 has_modules;       // the launch's graphs compose other graphs (module tasks)
     u32 steal_backoff_ns;  // longest sleep of a thief whose round found nothing (0 = 512)
     u32 keep_idle;         // 1: the kept backlog grows with the block's idle warps
-    u32 pad6;
+    u32 hand_batch;        // 1: a step's whole output (<= batch_max) stays with its warp while the ring is empty
     u32 *thief_slots;      // max_thieves words, each on its own 128-byte line
     u64 time_limit_ns;
     u64 *trace;            // TG_OPT_TRACE: per task {start ns, publish ns} (may be null)

@@ -1374,9 +1374,19 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         // ---- a warp whose step produced at most kHandMax activations runs
         // them itself next (a chain never leaves the warp); wider output is
         // published to the block's ring / public deque, where it merges with
-        // the siblings' work and spreads
+        // the siblings' work and spreads.  With hand_batch a whole step's
+        // output up to batch_max stays with the warp while the block's ring
+        // is empty (no sibling waits for work there): on a wavefront it then
+        // skips the publication and the pickup of every hop.
         {
-            const u32 keep = ns <= kHandMax ? ns : 0u;
+            u32 keep = ns <= kHandMax ? ns : 0u;
+            if (p.hand_batch && keep == 0u && ns <= (u32)bmax) {
+                u32 lsz = 0;
+                if (lane == 0)
+                    lsz = ring_size<true>(w.local);
+                if (__shfl_sync(kFull, lsz, 0) == 0u)
+                    keep = ns;
+            }
             __syncwarp();
             hand = (u32)lane < keep ? my_stage[lane] : kEmpty;
             nh = (int)keep;

@@ -275,6 +275,7 @@ extern "C" int tg_run_noalloc(uint32_t n_nodes, const uint8_t *kinds, const uint
     p.idle_sleep_ns = 256;
     p.steal_backoff_ns = 512;
     p.keep_idle = 0;
+    p.hand_batch = 0;
     p.max_thieves = kNaThieves;
     p.thief_slots = (u32 *)(base + kOffThief);
     p.time_limit_ns = 10ull * 1000 * 1000 * 1000;

@@ -54,7 +54,7 @@ class Executor:
     opts: any tg_ctx_opts field (worker_blocks, warps_per_block, deque_depth,
     steal_policy, max_steal, smem_ring, flags, idle_sleep_ns, max_thieves,
     batch_max, local_keep, thief_mode, time_limit_ns, exec_cap,
-    mem_budget_bytes, max_nodes, max_edges, steal_backoff_ns, keep_idle)."""
+    mem_budget_bytes, max_nodes, max_edges, steal_backoff_ns, keep_idle, hand_batch)."""
 
     def __init__(self, arena_bytes: int = 1 << 30, stream=None, **opts):
         import torch

@@ -119,7 +119,7 @@ def test_launch_geometry_variants_are_exact(ex):
         for geo in (dict(warps_per_block=4, worker_blocks=148, steal_policy=1, max_steal=2, max_thieves=4),
                     dict(warps_per_block=16, deque_depth=256, max_thieves=64),
                     dict(steal_backoff_ns=4096, idle_sleep_ns=1024),
-                    dict(steal_backoff_ns=32, worker_blocks=296, warps_per_block=8),
+                    dict(steal_backoff_ns=32, worker_blocks=296, warps_per_block=8, hand_batch=1),
                     dict(worker_blocks=1, warps_per_block=1)):
             ex.set_launch(**geo)
             b = ex.batch(hs)

@@ -283,7 +283,8 @@ def test_adaptive_thieves_finish_a_wide_wavefront():
     from paper_2004_10908_b300 import Executor
     g = w.config2b(seed=2, side=192, rounds=64)
     ref = oracle.run(g)
-    for geo in (dict(thief_mode=1, local_keep=16, max_thieves=8), dict(thief_mode=1, local_keep=16, batch_max=8)):
+    for geo in (dict(thief_mode=1, local_keep=16, max_thieves=8), dict(thief_mode=1, local_keep=16, batch_max=8),
+                dict(hand_batch=1), dict(hand_batch=1, warps_per_block=4, worker_blocks=148)):
         with Executor(arena_bytes=1 << 29, time_limit_ns=5_000_000_000, **geo) as e:
             for _ in range(3):
                 gh = e.graph(g)
@@ -358,7 +359,8 @@ def test_looping_graphs_never_report_a_false_race():
              [w.nested_loops(s) for s in range(3)]
     refs = [oracle.run(g) for g in graphs]
     for geo in (dict(), dict(warps_per_block=4, worker_blocks=592), dict(warps_per_block=8, batch_max=8),
-                dict(keep_idle=1), dict(keep_idle=1, warps_per_block=4, worker_blocks=296, local_keep=16)):
+                dict(keep_idle=1), dict(keep_idle=1, warps_per_block=4, worker_blocks=296, local_keep=16),
+                dict(hand_batch=1), dict(hand_batch=1, keep_idle=1, batch_max=8)):
         with Executor(arena_bytes=1 << 29, **geo) as ex:
             hs = [ex.graph(g) for g in graphs]
             for _ in range(8):
