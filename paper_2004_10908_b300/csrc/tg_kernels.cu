@@ -434,18 +434,22 @@ __device__ __forceinline__ T ld_imm(const T *ptr)
 
 // Stage the new activations of the lanes with `has` in the warp's buffer;
 // a full buffer is published early (its owners keep their flags meanwhile).
-__device__ __forceinline__ void stage(WarpCtx &w, u64 *buf, u32 &ns, bool has, u64 ent, int lane, u32 &spill_ctr)
+__device__ __forceinline__ void stage(WarpCtx &w, u64 *buf, u32 &ns, bool has, u64 ent, int lane, u32 &spill_ctr,
+                                      u64 *pe_resv = nullptr)
 {
     const u32 m = __ballot_sync(kFull, has);
     if (m == 0)
         return;
     const u32 k = (u32)__popc(m);
     if (ns + k > kStage) {
+        // pe_resv: the activations are reserved here, as they leave the warp
+        if (pe_resv && lane == 0)
+            atomicAdd(pe_resv, (u64)ns);
         fence_acq_rel_cta();   // the pending-count reservation first
         __syncwarp();
         for (u32 i = 0; i < ns; i += 32u) {
             const bool h = i + (u32)lane < ns;
-            emit(w, h, h ? buf[i + lane] : 0ull, lane, spill_ctr);
+            emit(w, h, h ? buf[i + lane] : 0ull, lane, spill_ctr, pe_resv);
         }
         ns = 0;
         __syncwarp();
@@ -1097,12 +1101,17 @@ __device__ __forceinline__ void sched_body(const KParams &p)
 
         const bool run = act && c_status == 0;
         const u32 U = run ? ((kind == TG_STATIC || cont) ? succ_cnt : (detached ? succ_cnt + 1u : 1u)) : 0u;
+        // acyclic launches of one graph reserve pending counts only for the
+        // activations that leave the warp, as they leave it
+        u64 *const pe_lazy = kAcyc ? &p.descs[p.single_gid].pe : nullptr;
         // reserve the pending count of every activation this warp may push
         // before any of them becomes visible (a fence precedes publication)
         if (single) {
-            const u32 sumU = __reduce_add_sync(kFull, U);
-            if (lane == 0 && sumU)
-                atomicAdd(&p.descs[p.single_gid].pe, (u64)sumU);
+            if (!kAcyc) {
+                const u32 sumU = __reduce_add_sync(kFull, U);
+                if (lane == 0 && sumU)
+                    atomicAdd(&p.descs[p.single_gid].pe, (u64)sumU);
+            }
         } else {
             // lanes grouped by graph (lanes that run nothing form one more
             // group); each group's lowest lane adds the group's sum
@@ -1133,6 +1142,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         // all of its checks returned, and only then are the activations
         // published.  A task that pushes itself hands its flag on.
         u32 ns = 0;              // staged entries (warp-uniform)
+        u32 kept = 0;            // of them, kept by the warp for its next step
         u32 racy = kEmpty32;     // graph whose activation found a target in flight
         u32 mp = 0;              // activations this lane's task pushed (own-lane part)
         bool keep_self = false;  // this lane's task pushed itself
@@ -1190,7 +1200,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                     const u32 t = s_[j] & ~kSoleBit;
                     const u64 ent = (s_[j] & kSoleBit) ? (((u64)x << 32) | (u64)t)
                                                        : (((u64)((u32)(old_[j] >> 32) + x) << 32) | kStrongBit | (u64)t);
-                    stage(w, my_stage, ns, has_[j], ent, lane, st_spill);
+                    stage(w, my_stage, ns, has_[j], ent, lane, st_spill, pe_lazy);
                     if (fl_[j] & kInflight)
                         racy = gid;
                 }
@@ -1250,7 +1260,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                     fetch_flat(base + 32u * kRelUnroll);
 #pragma unroll
                 for (int j = 0; j < kRelUnroll; ++j)
-                    stage(w, my_stage, ns, has_[j], ent_[j], lane, st_spill);
+                    stage(w, my_stage, ns, has_[j], ent_[j], lane, st_spill, pe_lazy);
             }
 #pragma unroll
             for (int j = 0; j < kRelUnroll; ++j)
@@ -1299,7 +1309,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                                   dg));
             if (kServe || any_enter || (ns > kHandMax && !acyclic))
                 fence_acq_rel_gpu();
-            else if (ns > kHandMax)
+            else if (ns > kHandMax && !kAcyc)
                 fence_acq_rel_cta();
         } else if (any_enter) {
             fence_acq_rel_gpu();
@@ -1380,6 +1390,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         // skips the publication and the pickup of every hop.
         {
             u32 keep = ns <= kHandMax ? ns : 0u;
+            kept = 0u;
             if (p.hand_batch && keep == 0u && ns <= (u32)bmax) {
                 u32 lsz = 0;
                 if (lane == 0)
@@ -1390,8 +1401,15 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             __syncwarp();
             hand = (u32)lane < keep ? my_stage[lane] : kEmpty;
             nh = (int)keep;
-            if (ns > keep)
-                publish<kIdle>(w, my_stage + keep, ns - keep, lane, st_spill, kAcyc ? &p.descs[p.single_gid].pe : nullptr);
+            kept = keep;
+            if (ns > keep) {
+                if (kAcyc) {
+                    if (lane == 0)
+                        atomicAdd(pe_lazy, (u64)(ns - keep));
+                    fence_acq_rel_cta();
+                }
+                publish<kIdle>(w, my_stage + keep, ns - keep, lane, st_spill, pe_lazy);
+            }
             __syncwarp();
         }
 
@@ -1404,7 +1422,9 @@ __device__ __forceinline__ void sched_body(const KParams &p)
                 const u32 sumP = __reduce_add_sync(kFull, P);
                 const u32 sumU = __reduce_add_sync(kFull, U);
                 if (lane == 0 && E) {
-                    const long long d = (long long)sumP - (long long)sumU - (long long)E;
+                    // (kAcyc: what left the warp was reserved as it left)
+                    const long long d = kAcyc ? (long long)kept - (long long)E
+                                              : (long long)sumP - (long long)sumU - (long long)E;
                     pend_delta = ((u64)E << 32) + (u64)d;   // (no continuations without modules)
                     if (kAcyc) {
                         // every task runs at most once, so the cap needs no
