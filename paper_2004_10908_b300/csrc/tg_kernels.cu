@@ -615,6 +615,9 @@ __device__ __forceinline__ void sched_body(const KParams &p)
     // activations this warp kept for itself (lanes [0, nh) of `hand`)
     u64 hand = kEmpty;
     int nh = 0;
+    // kAcyc: the records of the kept activations, loaded when they were kept
+    uint4 hand_imm = make_uint4(0u, 0u, 0u, 0u);
+    bool hand_pre = false;
     // per-lane cache of the lane's graph descriptor; the status word is
     // re-read every 16 activations, so a poisoned graph drains soon after
     u32 c_gid = kEmpty32, c_seed = 0, c_cap = 0, c_age = 0, c_base = 0;
@@ -640,10 +643,12 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         u64 e = kEmpty;
         int k = 0;
         mark(-1);
+        bool pre_now = false;
         if (nh) {
             e = hand;
             k = nh;
             nh = 0;
+            pre_now = hand_pre;
             st_hand++;
             from = TG_TRACE_FROM_HAND;
         } else {
@@ -962,7 +967,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         uint2 stt = make_uint2(0, 0);
         u32 gid = 0;
         if (act) {
-            imm = ld_imm<kServe>(reinterpret_cast<const uint4 *>(&p.slots[u]));
+            imm = (kAcyc && pre_now) ? hand_imm : ld_imm<kServe>(reinterpret_cast<const uint4 *>(&p.slots[u]));
             // (an acyclic launch runs each task once: its count and digest are 0)
             stt = acyclic ? make_uint2(0u, 0u) : __ldcg(reinterpret_cast<const uint2 *>(&p.slots[u].cnt));
             gid = single ? p.single_gid : ld_imm<kServe>(&p.chunk_gid[u >> kChunkShift]);
@@ -1401,6 +1406,15 @@ __device__ __forceinline__ void sched_body(const KParams &p)
             __syncwarp();
             hand = (u32)lane < keep ? my_stage[lane] : kEmpty;
             nh = (int)keep;
+            // kAcyc: the kept tasks' records are loaded now, their latency
+            // hidden behind the rest of this step (records are immutable
+            // while the graph runs)
+            hand_pre = false;
+            if (kAcyc && keep) {
+                if ((u32)lane < keep)
+                    hand_imm = ld_imm<kServe>(reinterpret_cast<const uint4 *>(&p.slots[(u32)hand & kIdMask]));
+                hand_pre = true;
+            }
             kept = keep;
             if (ns > keep) {
                 if (kAcyc) {
