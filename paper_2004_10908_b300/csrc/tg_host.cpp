@@ -1790,8 +1790,8 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
     const int batch_c[] = {8, 16, 24, 32};
     const int keep_c[] = {16, 32, 64, 128, 512};
     const int tmode_c[] = {0, 1};
-    const int backoff_c[] = {512, 4096};
-    const int idle_c[] = {256, 1024};
+    const int backoff_c[] = {128, 512, 4096};
+    const int idle_c[] = {128, 256, 1024};
     const int keep_idle_c[] = {0, 1};
     const int hand_batch_c[] = {0, 1};
     auto try_knob = [&](auto setter, const int *vals, int nv) -> int {
@@ -1832,8 +1832,8 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
             (rc = try_knob([](tg_ctx_opts &o, int v) { o.keep_idle = v; }, keep_idle_c, 2)) != TG_OK ||
             (rc = try_knob([](tg_ctx_opts &o, int v) { o.hand_batch = v; }, hand_batch_c, 2)) != TG_OK ||
             (rc = try_knob([](tg_ctx_opts &o, int v) { o.thief_mode = v; }, tmode_c, 2)) != TG_OK ||
-            (rc = try_knob([](tg_ctx_opts &o, int v) { o.steal_backoff_ns = (u32)v; }, backoff_c, 2)) != TG_OK ||
-            (rc = try_knob([](tg_ctx_opts &o, int v) { o.idle_sleep_ns = (u32)v; }, idle_c, 2)) != TG_OK)
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.steal_backoff_ns = (u32)v; }, backoff_c, 3)) != TG_OK ||
+            (rc = try_knob([](tg_ctx_opts &o, int v) { o.idle_sleep_ns = (u32)v; }, idle_c, 3)) != TG_OK)
             return rc;
         if (best_t >= pass_t)
             break;
