@@ -37,8 +37,10 @@ Measured in the same run and reported beside it:
             oracle (all at 1k, 1 in 50 above), the plain form (one launch per
             request) beside it at rates it sustains, graph creation cost
   e2e       the headline workload through the C-ABI with host buffers:
-            ingest + validate + pack + upload, submit, wait, download every
-            result; each graph is ingested while the previous one runs
+            inputs copied from pinned host memory, validated and packed on
+            the device (tg_graph_create_dev), submit, wait, download every
+            result; each graph is ingested while the previous one runs; the
+            same with the host packer (tg_graph_create) beside it
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
                   [--small] [--batched-graphs N] [--skip-batched] [--skip-serving] [--skip-extras]
@@ -270,17 +272,36 @@ def headline(ex, graphs, args, torch, B, world=1):
     return step_ms, per_graph, clk.summary(), stats, tuned
 
 
-def e2e(ex, graphs, reps):
+def e2e(ex, graphs, reps, device_pack=True):
     """The user's path, as a stream of graphs through the public API: create
     (ingest, validate, pack, upload), take the tuned geometry from the tuning
     cache (no runs), submit, wait, read every result back, destroy.  As a
     user pipelines the asynchronous API, each graph is ingested while the
     previous one runs, step after step.  A step is every headline graph once
     -- ingested, uploaded, run and read back -- and its time is the stream's
-    wall time over its steps."""
+    wall time over its steps.  device_pack: tg_graph_create_dev, which copies
+    the inputs (held in pinned host memory, as such a user holds them) to
+    the device and validates and packs them there; else tg_graph_create,
+    which packs on one host core and uploads the packed graph."""
+    import torch
     h2d = d2h = 0
     parts = {"create_pack": 0.0, "create_upload": 0.0, "create_other": 0.0, "wait": 0.0, "read_back": 0.0,
              "other": 0.0}
+    keep = []
+    inputs = []
+    for g in graphs:
+        if not device_pack:
+            inputs.append(g)
+            continue
+        class _Pinned:
+            pass
+        p = _Pinned()
+        for k in ("kinds", "params", "src", "dst"):
+            t = torch.from_numpy(np.ascontiguousarray(getattr(g, k))).pin_memory()
+            keep.append(t)
+            setattr(p, k, t.numpy())
+        p.seed, p.name = g.seed, g.name
+        inputs.append(p)
 
     def finish(gh, ticket):
         t1 = time.perf_counter()
@@ -292,26 +313,44 @@ def e2e(ex, graphs, reps):
         parts["wait"] += (t2 - t1) * 1e3
         parts["read_back"] += (t3 - t2) * 1e3
 
+    # one untimed step first: the context's first creation and read-back
+    # allocate their scratch
+    for gin in inputs:
+        gh = ex.graph(gin, device_pack=device_pack)
+        ex.autotune(gh, cache_path=TUNE_CACHE)
+        assert ex.wait(ex.submit(gh)) == 0
+        ex.result(gh)
+        gh.destroy()
     pending = None
     t0 = time.perf_counter()
     for _ in range(reps):
-        for g in graphs:
+        for g, gin in zip(graphs, inputs):
             t1 = time.perf_counter()
-            gh = ex.graph(g)
+            gh = ex.graph(gin, device_pack=device_pack)
             inf = gh.info()
             dt = (time.perf_counter() - t1) * 1e3
             parts["create_pack"] += inf["pack_ns"] / 1e6
             parts["create_upload"] += inf["upload_ns"] / 1e6
             parts["create_other"] += dt - (inf["pack_ns"] + inf["upload_ns"]) / 1e6
             ex.autotune(gh, cache_path=TUNE_CACHE)
+            # queued behind the previous graph's run, whose results are then
+            # read while this one runs
+            ticket = ex.submit(gh)
             if pending is not None:
                 finish(*pending)
-            pending = (gh, ex.submit(gh))
-            # copied per graph: successor lists and sources, task records,
-            # chunk table, descriptor; back: outputs and the packed
-            # count/digest words
-            h2d += g.m * 4 + g.n * 4 + 32 * g.n + 64 + ((g.n + 255) // 256) * 4
-            d2h += g.n * 4 + g.n * 8
+            pending = (gh, ticket)
+            if device_pack:
+                # copied per graph: kinds, parameters, sources and targets of
+                # the edges; back: the validation words, then the outputs and
+                # the packed count/digest words
+                h2d += g.n * 5 + g.m * 8
+                d2h += 16 + g.n * 4 + g.n * 8
+            else:
+                # copied per graph: successor lists and sources, task records,
+                # chunk table, descriptor; back: outputs and the packed
+                # count/digest words
+                h2d += g.m * 4 + g.n * 4 + 32 * g.n + 64 + ((g.n + 255) // 256) * 4
+                d2h += g.n * 4 + g.n * 8
     finish(*pending)
     total = (time.perf_counter() - t0) * 1e3 / reps
     parts = {k: v / reps for k, v in parts.items()}
@@ -422,12 +461,13 @@ def condition_heavy(Executor, torch, peaks, atom_ceiling):
 
 
 def creation_cost(Executor):
-    """Host cost of graph creation the way the paper's Table 3 reports it
+    """Cost of graph creation the way the paper's Table 3 reports it
     (time per task and per edge, amortised over many): validation + packing
     of 1,000,000 tasks without edges, then of the same tasks with 8,000,000
     edges (each task 8 successors in the next 1,000-task level); the
     difference over the edge count is the cost per edge.  The upload to the
-    device is reported apart."""
+    device is reported apart.  Host packer (tg_graph_create), then the
+    device path (tg_graph_create_dev)."""
     n, width, deg = 1_000_000, 1000, 8
     rng = np.random.default_rng(7)
     v = np.arange(n - width, dtype=np.int64)
@@ -435,24 +475,42 @@ def creation_cost(Executor):
     dst = ((v // width + 1) * width)[:, None] + rng.integers(0, width, (v.shape[0], deg))
     kinds = np.zeros(n, np.uint8)
     params = np.full(n, 16, np.uint32)
+    import torch
+
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
     rows = {}
     with Executor(arena_bytes=2 << 30) as ex:
-        for name, s_, d_ in (("tasks", np.zeros(0, np.uint32), np.zeros(0, np.uint32)),
-                             ("tasks_edges", src.astype(np.uint32), dst.reshape(-1).astype(np.uint32))):
-            best = None
-            for _ in range(3):
-                h = ex.create(kinds, params, s_, d_, 0, name=name)
-                inf = h.info()
-                h.destroy()
-                if best is None or inf["pack_ns"] < best["pack_ns"]:
-                    best = inf
-            rows[name] = (best, int(s_.shape[0]))
-    t, te = rows["tasks"][0], rows["tasks_edges"][0]
-    m = rows["tasks_edges"][1]
-    return {"tasks": n, "edges": m, "pack_ns_per_task": t["pack_ns"] / n,
-            "pack_ns_per_edge": (te["pack_ns"] - t["pack_ns"]) / m,
-            "upload_ns_per_task": t["upload_ns"] / n, "upload_ns_per_edge": (te["upload_ns"] - t["upload_ns"]) / m,
-            "paper": "61 ns/task, 14 ns/edge (Table 3, one host thread of a 40-core machine)"}
+        for dev in (False, True):
+            for name, s_, d_ in (("tasks", np.zeros(0, np.uint32), np.zeros(0, np.uint32)),
+                                 ("tasks_edges", src.astype(np.uint32), dst.reshape(-1).astype(np.uint32))):
+                ins = [kinds, params, s_, d_]
+                if dev:
+                    ins = [pinned(a) for a in ins]
+                    keep, ins = ins, [t.numpy() for t in ins]
+                best = None
+                for _ in range(3):
+                    h = ex.create(*ins, 0, name=name, device_pack=dev)
+                    inf = h.info()
+                    h.destroy()
+                    if best is None or inf["pack_ns"] < best["pack_ns"]:
+                        best = inf
+                rows[(dev, name)] = (best, int(s_.shape[0]))
+
+    def per(dev):
+        t, te = rows[(dev, "tasks")][0], rows[(dev, "tasks_edges")][0]
+        m = rows[(dev, "tasks_edges")][1]
+        return {"pack_ns_per_task": t["pack_ns"] / n, "pack_ns_per_edge": (te["pack_ns"] - t["pack_ns"]) / m,
+                "upload_ns_per_task": t["upload_ns"] / n,
+                "upload_ns_per_edge": (te["upload_ns"] - t["upload_ns"]) / m}
+
+    out = {"tasks": n, "edges": rows[(False, "tasks_edges")][1], **per(False),
+           "paper": "61 ns/task, 14 ns/edge (Table 3, one host thread of a 40-core machine)"}
+    # tg_graph_create_dev: device time of validation + pack, and of the
+    # input copies from pinned host memory
+    out["device_pack"] = per(True)
+    return out
 
 
 def thief_policies(Executor):
@@ -989,6 +1047,7 @@ def run_b300(args):
         joins += int((sin[g.dst.astype(np.int64)] > 1).sum())
     atomics_per_launch = joins + 2 * stats["warp_iters"]
     e2e_ms, h2d, d2h, e2e_parts = e2e(ex, graphs, max(3, min(args.steps, 6)))
+    e2e_host_ms, _, _, e2e_host_parts = e2e(ex, graphs, 3, device_pack=False)
     ex.close()
     floor_ns = sum(c["floor_ms"] for c in crit.values()) * 1e6
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
@@ -1000,7 +1059,12 @@ def run_b300(args):
         "config": {"workload": WORKLOAD, "graphs": [g.name for g in graphs], "tasks_per_step": execs_per_step,
                    "l2": "flushed between steps (512 MB write)", "launch_geometry": tuned},
         "e2e": {"value": execs_per_step / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "host_ms_per_step": e2e_parts},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "host_ms_per_step": e2e_parts,
+                "create": "tg_graph_create_dev (ingest, validation and pack on the device, inputs in pinned "
+                          "host memory)",
+                "host_pack": {"value": execs_per_step / (e2e_host_ms / 1000.0), "ms_per_step": e2e_host_ms,
+                              "host_ms_per_step": e2e_host_parts,
+                              "create": "tg_graph_create (packed on one host core, then uploaded)"}},
         # the scheduler kernel is bound by its graphs' dependency chains: the
         # ceiling is every graph at its dependency floor (its longest path's
         # payloads back to back, measured in the same run); the bandwidth,

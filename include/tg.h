@@ -182,6 +182,24 @@ int tg_ctx_destroy(tg_ctx *ctx);
 int tg_graph_create(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
                     uint32_t n_edges, const uint32_t *src, const uint32_t *dst,
                     const uint8_t *weak, uint32_t seed, tg_graph **out);
+/* As tg_graph_create (same arguments, host pointers; same statuses in the
+ * same order; the same packed graph), with ingest, validation and packing
+ * done on the device (Task Graph Representation, and the successor order
+ * that Algorithm 8's condition dispatch indexes): the inputs are copied to
+ * the device -- from pinned memory asynchronously, from pageable memory
+ * through the driver's staging -- then the degrees are counted, the limits
+ * checked, the edges sorted stably by source task (insertion order within
+ * each task) and the records, successor lists and source list written.
+ * Graphs with module or subflow tasks are refused (TG_ERR_INVALID: they use
+ * tg_graph_create_composed).  The context keeps device scratch of about
+ * 29 bytes per task and 25 per edge, allocated on first use and grown when a
+ * larger graph comes (TG_ERR_BUDGET if that allocation fails); it is freed
+ * with the context.  Uses the side stream; complete when the call returns.
+ * tg_graph_get_info: pack_ns = device time of validation and packing,
+ * upload_ns = device time of the input copies. */
+int tg_graph_create_dev(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
+                        uint32_t n_edges, const uint32_t *src, const uint32_t *dst,
+                        const uint8_t *weak, uint32_t seed, tg_graph **out);
 /* As tg_graph_create, with module tasks (Composable Tasking, "composed_of")
  * and subflow tasks (Dynamic Tasking): modules[n_nodes] names, for every
  * TG_MODULE task, the graph it composes and, for every TG_SUBFLOW task, the
@@ -291,8 +309,12 @@ int tg_serve_replay(tg_ctx *ctx, tg_graph *const *templates, uint32_t n_template
 int tg_cancel(tg_ctx *ctx);
 
 /* Copy the per-task results of g's last run to host arrays of n entries
- * (any pointer may be NULL); total_execs = sum of cnt.  Synchronises the
- * context stream.  (The paper's tasks keep their results in user data; here
+ * (any pointer may be NULL); total_execs = sum of cnt.  Waits for g's last
+ * launch only (a graph submitted after g may run meanwhile; a graph that
+ * other graphs compose waits for the context stream), and reads on the side
+ * stream through a device buffer of 8 bytes per task that the context
+ * allocates on first use (TG_ERR_BUDGET if it cannot); while the resident
+ * server runs, the records are read directly.  (The paper's tasks keep their results in user data; here
  * every task's last output, execution count and digest stay in the graph's
  * device state until its next run.)  Results are read by graph, not by
  * ticket: a graph holds the state of its last run, while a ticket only

@@ -8,7 +8,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libtg.so")
 SOURCES = [os.path.join(CSRC, "tg_host.cpp"), os.path.join(CSRC, "tg_kernels.cu"),
-           os.path.join(CSRC, "tg_noalloc.cu"), os.path.join(CSRC, "tg_result.cu")]
+           os.path.join(CSRC, "tg_noalloc.cu"), os.path.join(CSRC, "tg_result.cu"),
+           os.path.join(CSRC, "tg_pack.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "tg_internal.h"), os.path.join(ROOT, "include", "tg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -81,6 +81,7 @@ SIGNATURES = {
                                      ctypes.POINTER(_vp)]),
     "tg_ctx_destroy": (ctypes.c_int, [_vp]),
     "tg_graph_create": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, ctypes.POINTER(_vp)]),
+    "tg_graph_create_dev": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, ctypes.POINTER(_vp)]),
     "tg_graph_autotune": (ctypes.c_int, [_vp, _vp, _u32, ctypes.c_char_p, ctypes.POINTER(tg_ctx_opts),
                                          ctypes.POINTER(_u64)]),
     "tg_graph_create_composed": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, _vp,
@@ -174,6 +175,21 @@ def tg_graph_create(ctx, kinds, params, src, dst, seed=0, weak=None):
     out = _vp()
     st = load().tg_graph_create(_vp(ctx), k.shape[0], kp, pp, s.shape[0], sp, dp, wp, seed & 0xFFFFFFFF,
                                 ctypes.byref(out))
+    return st, (out.value if st == TG_OK else None)
+
+
+def tg_graph_create_dev(ctx, kinds, params, src, dst, seed=0, weak=None):
+    """As tg_graph_create, packed on the device.  Returns (status, handle)."""
+    k, kp = _arr(kinds, np.uint8)
+    p, pp = _arr(params, np.uint32)
+    s, sp = _arr(src, np.uint32)
+    d, dp = _arr(dst, np.uint32)
+    wp = None
+    if weak is not None:
+        w, wp = _arr(weak, np.uint8)
+    out = _vp()
+    st = load().tg_graph_create_dev(_vp(ctx), k.shape[0], kp, pp, s.shape[0], sp, dp, wp, seed & 0xFFFFFFFF,
+                                    ctypes.byref(out))
     return st, (out.value if st == TG_OK else None)
 
 

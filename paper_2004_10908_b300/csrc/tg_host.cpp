@@ -215,6 +215,15 @@ struct tg_ctx {
     std::map<u64, Submission> subs;
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
     bool timed = false;
+    // tg_graph_create_dev: device scratch (grown on demand), the validation
+    // words' pinned copy, events around the input copies and the pack
+    char *pk_scratch = nullptr;
+    size_t pk_bytes = 0;
+    u32 *h_pkflags = nullptr;
+    cudaEvent_t pk_ev[3] = {nullptr, nullptr, nullptr};
+    // tg_result_copy: the packed counts and digests (grown on demand)
+    u64 *d_rb = nullptr;
+    size_t rb_bytes = 0;
 };
 
 namespace {
@@ -564,6 +573,15 @@ int tg_ctx_destroy(tg_ctx *c)
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
     }
+    if (c->pk_scratch)
+        cudaFree(c->pk_scratch);
+    if (c->d_rb)
+        cudaFree(c->d_rb);
+    if (c->h_pkflags)
+        cudaFreeHost(c->h_pkflags);
+    for (cudaEvent_t ev : c->pk_ev)
+        if (ev)
+            cudaEventDestroy(ev);
     if (c->ev_k0)
         cudaEventDestroy(c->ev_k0);
     if (c->ev_k1)
@@ -613,6 +631,47 @@ int tg_ctx_get_opts(const tg_ctx *c, tg_ctx_opts *o)
 }
 
 static bool is_cond(u32 kind) { return kind >= TG_COND_BRANCH && kind <= TG_COND_CONST; }
+
+// Pool space of a new graph: a chunk-aligned execution range, and in the
+// edge pool its successor lists (a module task's list led by the slot id of
+// the graph it composes) and its sources; a graph slot; the budget.
+static int graph_alloc(tg_ctx *c, u32 n, u32 m, u32 n_mod, u32 n_src, u32 n_cond, u32 seed, tg_graph **out)
+{
+    const u64 n_chunks = ((u64)n + kChunk - 1) >> kChunkShift;
+    const u64 bytes = n_chunks * kChunk * 36 + ((u64)m + n_mod + n_src) * 4;
+    if (c->used + bytes > c->budget || c->free_gids.empty())
+        return TG_ERR_BUDGET;
+    tg_graph *g = new (std::nothrow) tg_graph();
+    if (!g)
+        return TG_ERR_INVALID;
+    if (!c->nodes.alloc(n_chunks, g->chunk_off)) {
+        delete g;
+        return TG_ERR_BUDGET;
+    }
+    c->live_graphs.insert(g);
+    g->n_chunks = n_chunks;
+    g->node_off = g->chunk_off << kChunkShift;
+    g->edge_len = (u64)m + n_mod + n_src;
+    if (!c->edge_pool.alloc(g->edge_len, g->edge_off)) {
+        c->nodes.release(g->chunk_off, n_chunks);
+        c->live_graphs.erase(g);
+        delete g;
+        return TG_ERR_BUDGET;
+    }
+    g->gid = c->free_gids.back();
+    c->free_gids.pop_back();
+    c->used += bytes;
+    g->ctx = c;
+    g->n = n;
+    g->m = m;
+    g->n_src = n_src;
+    g->n_cond = n_cond;
+    g->n_mod = n_mod;
+    g->seed = seed;
+    g->bytes = bytes;
+    *out = g;
+    return TG_OK;
+}
 
 static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t *params, uint32_t m,
                         const uint32_t *src, const uint32_t *dst, const uint8_t *weak, uint32_t seed,
@@ -668,42 +727,10 @@ static int graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint3
     if (n_src == 0)
         return TG_ERR_NO_SOURCE;
 
-    // ---- pool space: a chunk-aligned execution range, and in the edge pool
-    // the successor lists and the sources
-    const u64 n_chunks = ((u64)n + kChunk - 1) >> kChunkShift;
-    const u64 bytes = n_chunks * kChunk * 36 + ((u64)m + n_mod + n_src) * 4;
-    if (c->used + bytes > c->budget || c->free_gids.empty())
-        return TG_ERR_BUDGET;
-    tg_graph *g = new (std::nothrow) tg_graph();
-    if (!g)
-        return TG_ERR_INVALID;
-    if (!c->nodes.alloc(n_chunks, g->chunk_off)) {
-        delete g;
-        return TG_ERR_BUDGET;
-    }
-    c->live_graphs.insert(g);
-    g->n_chunks = n_chunks;
-    g->node_off = g->chunk_off << kChunkShift;
-    // a module task's list is led by the slot id of the graph it composes
-    const u64 lead = (u64)m + n_mod + n_src;
-    g->edge_len = lead;
-    if (!c->edge_pool.alloc(g->edge_len, g->edge_off)) {
-        c->nodes.release(g->chunk_off, n_chunks);
-        c->live_graphs.erase(g);
-        delete g;
-        return TG_ERR_BUDGET;
-    }
-    g->gid = c->free_gids.back();
-    c->free_gids.pop_back();
-    c->used += bytes;
-    g->ctx = c;
-    g->n = n;
-    g->m = m;
-    g->n_src = n_src;
-    g->n_cond = n_cond;
-    g->n_mod = n_mod;
-    g->seed = seed;
-    g->bytes = bytes;
+    tg_graph *g = nullptr;
+    if (int ra = graph_alloc(c, n, m, n_mod, n_src, n_cond, seed, &g); ra != TG_OK)
+        return ra;
+    const u64 n_chunks = g->n_chunks;
 
     // ---- pack: successors in insertion order (graph-local ids), sources,
     // then the 32-byte task records (W = strong in-degree, cnt = dig = 0)
@@ -831,6 +858,89 @@ int tg_graph_create(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t 
                     const uint32_t *src, const uint32_t *dst, const uint8_t *weak, uint32_t seed, tg_graph **out)
 {
     return graph_create(c, n, kinds, params, m, src, dst, weak, seed, nullptr, out);
+}
+
+int tg_graph_create_dev(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t *params, uint32_t m,
+                        const uint32_t *src, const uint32_t *dst, const uint8_t *weak, uint32_t seed, tg_graph **out)
+{
+    if (!c || !out || n == 0 || !kinds || !params || (m && (!src || !dst)))
+        return TG_ERR_INVALID;
+    *out = nullptr;
+    // scratch for the copied inputs, the counts and the sort; an earlier
+    // call has finished with it (each call ends synchronised)
+    const size_t need = pack_scratch_bytes(n, m);
+    if (c->pk_bytes < need) {
+        if (c->pk_scratch) {
+            cudaFree(c->pk_scratch);
+            c->pk_scratch = nullptr;
+            c->pk_bytes = 0;
+        }
+        if (cudaMalloc((void **)&c->pk_scratch, need) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return TG_ERR_BUDGET;
+        }
+        c->pk_bytes = need;
+    }
+    if (!c->h_pkflags) {
+        TG_CUDA(cudaHostAlloc((void **)&c->h_pkflags, 256, cudaHostAllocDefault));
+        for (cudaEvent_t &ev : c->pk_ev)
+            TG_CUDA(cudaEventCreate(&ev));
+    }
+    PackBufs b;
+    pack_carve(c->pk_scratch, n, m, b);
+    cudaStream_t st = c->side;
+    TG_CUDA(cudaEventRecord(c->pk_ev[0], st));
+    TG_CUDA(cudaMemcpyAsync(b.kinds, kinds, n, cudaMemcpyHostToDevice, st));
+    TG_CUDA(cudaMemcpyAsync(b.params, params, (size_t)4 * n, cudaMemcpyHostToDevice, st));
+    if (m) {
+        TG_CUDA(cudaMemcpyAsync(b.src, src, (size_t)4 * m, cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemcpyAsync(b.dst, dst, (size_t)4 * m, cudaMemcpyHostToDevice, st));
+        if (weak)
+            TG_CUDA(cudaMemcpyAsync(b.weak, weak, m, cudaMemcpyHostToDevice, st));
+    }
+    TG_CUDA(cudaEventRecord(c->pk_ev[1], st));
+    TG_CUDA(pack_validate(b, n, m, weak != nullptr, st));
+    TG_CUDA(cudaMemcpyAsync(c->h_pkflags, b.flags, PK_FLAGS * sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TG_CUDA(cudaStreamSynchronize(st));
+    // the host packer's order of statuses
+    const u32 *f = c->h_pkflags;
+    if (f[PK_INVALID])
+        return TG_ERR_INVALID;
+    if (f[PK_EDGE_KIND])
+        return TG_ERR_EDGE_KIND;
+    if (f[PK_NSRC] == 0u)
+        return TG_ERR_NO_SOURCE;
+    tg_graph *g = nullptr;
+    if (int ra = graph_alloc(c, n, m, 0u, f[PK_NSRC], f[PK_NCOND], seed, &g); ra != TG_OK)
+        return ra;
+    PackDest d{};
+    d.slots = c->slots + g->node_off;
+    d.edges = c->edges + g->edge_off;
+    d.edge_base = (u32)g->edge_off;
+    d.chunk_gid = c->chunk_gid + g->chunk_off;
+    d.n_chunks = (u32)g->n_chunks;
+    d.gid = g->gid;
+    d.desc = c->descs + g->gid;
+    d.seed = seed;
+    d.node_off = (u32)g->node_off;
+    d.n_src = g->n_src;
+    d.exec_cap = (u32)std::min<u64>(c->opts.exec_cap, 0xFFFFFFFFull);
+    cudaError_t e = pack_build(b, n, m, d, st);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(c->pk_ev[2], st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        tg_graph_destroy(c, g);
+        return TG_ERR_CUDA;
+    }
+    float up = 0.f, pk = 0.f;
+    if (cudaEventElapsedTime(&up, c->pk_ev[0], c->pk_ev[1]) == cudaSuccess)
+        g->upload_ns = (u64)((double)up * 1e6);
+    if (cudaEventElapsedTime(&pk, c->pk_ev[1], c->pk_ev[2]) == cudaSuccess)
+        g->pack_ns = (u64)((double)pk * 1e6);
+    *out = g;
+    return TG_OK;
 }
 
 int tg_graph_create_composed(tg_ctx *c, uint32_t n, const uint8_t *kinds, const uint32_t *params, uint32_t m,
@@ -1160,23 +1270,38 @@ int tg_result_copy(tg_ctx *c, const tg_graph *g, uint32_t *out, uint32_t *cnt, u
 {
     if (!c || !g || g->ctx != c)
         return TG_ERR_INVALID;
-    if (!c->serving)
-        TG_CUDA(cudaStreamSynchronize(c->stream));
-    if (!c->serving && c->inj_cap >= g->n) {
-        // Between launches: the counts and digests are packed on the device
-        // (8 bytes per task instead of the 32-byte record), in the injection
-        // queue's memory, which is cleared before the next scheduler launch;
-        // both arrays come back through the pinned staging buffer.
+    if (!c->serving) {
+        // After the graph's own last launch -- not the whole context stream,
+        // where a graph submitted later may run meanwhile -- the counts and
+        // digests are packed on the device (8 bytes per task instead of the
+        // 32-byte record) into a read-back buffer of the context, and both
+        // arrays come back through the pinned staging buffer, all on the
+        // side stream.
         const size_t out_bytes = (size_t)g->n * 4, word_bytes = (size_t)g->n * 8;
         int rs = ensure_stage(c, out_bytes + word_bytes);
         if (rs != TG_OK)
             return rs;
-        c->dirty = true;
-        TG_CUDA(launch_result_gather(c->slots, (u32)g->node_off, g->n, c->inj, c->stream));
-        TG_CUDA(cudaMemcpyAsync(c->h_stage, c->inj, word_bytes, cudaMemcpyDeviceToHost, c->stream));
+        if (c->rb_bytes < word_bytes) {
+            TG_CUDA(cudaStreamSynchronize(c->side));
+            if (c->d_rb)
+                cudaFree(c->d_rb);
+            c->d_rb = nullptr;
+            c->rb_bytes = 0;
+            if (cudaMalloc((void **)&c->d_rb, word_bytes) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return TG_ERR_BUDGET;
+            }
+            c->rb_bytes = word_bytes;
+        }
+        if (g->busy)
+            TG_CUDA(cudaStreamWaitEvent(c->side, g->busy, 0));
+        else if (g->n_refs || g->tmpl)
+            TG_CUDA(cudaStreamSynchronize(c->stream));   // it may run inside the launch of a graph composing it
+        TG_CUDA(launch_result_gather(c->slots, (u32)g->node_off, g->n, c->d_rb, c->side));
+        TG_CUDA(cudaMemcpyAsync(c->h_stage, c->d_rb, word_bytes, cudaMemcpyDeviceToHost, c->side));
         TG_CUDA(cudaMemcpyAsync(c->h_stage + word_bytes, c->outv + g->node_off, out_bytes, cudaMemcpyDeviceToHost,
-                                c->stream));
-        TG_CUDA(cudaStreamSynchronize(c->stream));
+                                c->side));
+        TG_CUDA(cudaStreamSynchronize(c->side));
         const u64 *hw = (const u64 *)c->h_stage;
         const u32 *ho = (const u32 *)(c->h_stage + word_bytes);
         u64 tot = 0;

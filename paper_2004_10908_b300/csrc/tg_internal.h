@@ -186,6 +186,32 @@ cudaError_t launch_instance_rearm(NodeSlot *slots, u64 src_off, u64 dst_off, u32
 // kernel, which waits for that launch's work -- until its time limit.
 cudaError_t preload_serving_kernels(cudaStream_t st);
 cudaError_t launch_capture_task(NodeSlot *slots, u32 *outv, const u32 *edges, u32 u, u32 node_off, cudaStream_t st);
+// tg_pack.cu: graph ingest, validation and CSR pack on the device.
+// flags[PK_INVALID] / [PK_EDGE_KIND]: a cause of that status was found;
+// flags[PK_NSRC]: sources; flags[PK_NCOND]: condition tasks.
+enum { PK_INVALID = 0, PK_EDGE_KIND, PK_NSRC, PK_NCOND, PK_FLAGS };
+struct PackBufs {          // device scratch, carved by pack_carve
+    u8 *kinds, *weak;      // the copied inputs
+    u32 *params, *src, *dst;
+    u32 *k1, *v1;          // the sort's second buffers
+    u32 *outdeg, *sin, *win, *is_src, *off, *srcpos;
+    u32 *flags, *hist, *sums;
+};
+struct PackDest {          // where the packed graph goes
+    NodeSlot *slots;       // the graph's first record
+    u32 *edges;            // its successor lists, then its sources
+    u32 edge_base;         // global edge-pool index of edges[0]
+    u32 *chunk_gid;        // its chunk-table entries
+    u32 n_chunks, gid;
+    GDesc *desc;
+    u32 seed, node_off, n_src, exec_cap;
+};
+size_t pack_scratch_bytes(u32 n, u32 m);
+void pack_carve(char *base, u32 n, u32 m, PackBufs &b);
+// steps 1-3 (statuses and counts into flags); the inputs are in b
+cudaError_t pack_validate(const PackBufs &b, u32 n, u32 m, bool weak, cudaStream_t st);
+// steps 4-5, after a validation that found nothing
+cudaError_t pack_build(const PackBufs &b, u32 n, u32 m, const PackDest &d, cudaStream_t st);
 // tg_result.cu: pack the count and digest of tasks [node_off, node_off + n) into dst[0, n)
 cudaError_t launch_result_gather(const NodeSlot *slots, u32 node_off, u32 n, u64 *dst, cudaStream_t st);
 

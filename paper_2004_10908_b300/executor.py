@@ -70,17 +70,20 @@ class Executor:
         self.ctx = B.tg_ctx_create(self.arena.data_ptr(), int(arena_bytes), self.stream.cuda_stream, o)
 
     # -- graphs -----------------------------------------------------------
-    def create(self, kinds, params, src, dst, seed=0, weak=None, name=""):
-        st, h = B.tg_graph_create(self.ctx, kinds, params, src, dst, seed, weak)
+    def create(self, kinds, params, src, dst, seed=0, weak=None, name="", device_pack=False):
+        """device_pack: ingest, validate and pack on the device (tg_graph_create_dev)."""
+        fn = B.tg_graph_create_dev if device_pack else B.tg_graph_create
+        st, h = fn(self.ctx, kinds, params, src, dst, seed, weak)
         if st != B.TG_OK:
-            raise B.TgError(st, f"tg_graph_create {name}")
+            raise B.TgError(st, f"{fn.__name__} {name}")
         return GraphHandle(self, h, len(kinds), len(src), name)
 
-    def graph(self, g, weak=None, modules=None):
+    def graph(self, g, weak=None, modules=None, device_pack=False):
         """Upload a workloads.Graph-like object (kinds, params, src, dst, seed).
-        modules: {task: GraphHandle} naming the graph each TG_MODULE task composes."""
+        modules: {task: GraphHandle} naming the graph each TG_MODULE task composes.
+        device_pack: ingest, validate and pack on the device (no modules)."""
         if modules is None:
-            return self.create(g.kinds, g.params, g.src, g.dst, g.seed, weak, getattr(g, "name", ""))
+            return self.create(g.kinds, g.params, g.src, g.dst, g.seed, weak, getattr(g, "name", ""), device_pack)
         st, h = B.tg_graph_create_composed(self.ctx, g.kinds, g.params, g.src, g.dst,
                                            {v: gh.handle for v, gh in modules.items()}, g.seed, weak)
         if st != B.TG_OK:
