@@ -192,7 +192,7 @@ int tg_graph_create(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const u
  * each task) and the records, successor lists and source list written.
  * Graphs with module or subflow tasks are refused (TG_ERR_INVALID: they use
  * tg_graph_create_composed).  The context keeps device scratch of about
- * 29 bytes per task and 25 per edge, allocated on first use and grown when a
+ * 29 bytes per task and 17 per edge, allocated on first use and grown when a
  * larger graph comes (TG_ERR_BUDGET if that allocation fails); it is freed
  * with the context.  Uses the side stream; complete when the call returns.
  * tg_graph_get_info: pack_ns = device time of validation and packing,
