@@ -118,3 +118,53 @@ def test_budget_is_checked_after_validation():
         bad = w.from_lists("bad_idx", [0, 0], [1, 1], [(0, 5)])
         st_d, d = B.tg_graph_create_dev(e.ctx, bad.kinds, bad.params, bad.src, bad.dst, 0)
         assert st_d == B.TG_ERR_INVALID
+
+
+def test_random_graphs_valid_and_invalid(ex):
+    """Random graphs, some with an error planted: the device path returns the
+    host packer's status, and for every graph created its packed graph."""
+    rng = np.random.default_rng(2024)
+    created = 0
+    for t in range(120):
+        n = int(rng.integers(1, 3000))
+        m = int(rng.integers(0, 4 * n + 1))
+        kinds = rng.choice([0, 0, 0, 1, 2, 3], size=n).astype(np.uint8)
+        params = (rng.integers(1, 40, n) | (rng.integers(1, 6, n) << 16) |
+                  (rng.integers(0, 4, n) << 24)).astype(np.uint32)
+        src = rng.integers(0, n, m).astype(np.uint32)
+        dst = rng.integers(0, n, m).astype(np.uint32)
+        # forward edges, so that sources exist; every condition gets a successor
+        lo, hi = np.minimum(src, dst), np.maximum(src, dst)
+        cv = np.nonzero((kinds >= 1) & (kinds <= 3))[0].astype(np.uint32)
+        src = np.concatenate([lo, cv]).astype(np.uint32)
+        dst = np.concatenate([hi, np.minimum(cv + 1, n - 1)]).astype(np.uint32)
+        m = len(src)
+        weak = None
+        fault = t % 6
+        if fault == 1 and m:
+            dst[rng.integers(0, m)] = n + int(rng.integers(0, 5))       # index out of range
+        elif fault == 2:
+            kinds[rng.integers(0, n)] = 9                                # unknown kind
+        elif fault == 3 and m:
+            weak = ((kinds[src] >= 1) & (kinds[src] <= 3)).astype(np.uint8)
+            if t % 12 == 3:
+                weak[rng.integers(0, m)] ^= 1                            # one edge kind flipped
+        elif fault == 4:
+            loops = np.nonzero(kinds == 2)[0]
+            if loops.size:
+                params[loops[0]] &= ~np.uint32(0xFF << 16)               # loop trip 0
+        elif fault == 5:
+            every = np.arange(n, dtype=np.uint32)                        # a self-edge on every task: no source
+            src, dst = np.concatenate([src, every]), np.concatenate([dst, every])
+        st_h, h = B.tg_graph_create(ex.ctx, kinds, params, src, dst, t, weak)
+        st_d, d = B.tg_graph_create_dev(ex.ctx, kinds, params, src, dst, t, weak)
+        try:
+            assert st_d == st_h, (t, B.STATUS_NAMES[st_d], B.STATUS_NAMES[st_h])
+            if st_h == B.TG_OK:
+                assert B.tg_graph_dot(ex.ctx, d) == B.tg_graph_dot(ex.ctx, h), t
+                created += 1
+        finally:
+            for x in (h, d):
+                if x is not None:
+                    B.tg_graph_destroy(ex.ctx, x)
+    assert created > 20
