@@ -563,8 +563,11 @@ def critical_path_trace(Executor, B, graphs, tuned):
     """One run of each headline graph at its tuned geometry with per-task
     trace records (TG_OPT_TRACE_TASKS: the lean scheduler variant still
     runs), read along the graph's critical path: how much of each hand-off
-    is the step and how much is waiting, by where the task was taken from."""
-    from paper_2004_10908_b300.trace import critical_path
+    is the step and how much is waiting, by where the task was taken from;
+    then step by step (duration by tasks in the step and by the steps of
+    the same block running at once) and level by level (layers of the
+    layered DAG, anti-diagonals of the wavefront)."""
+    from paper_2004_10908_b300.trace import critical_path, level_summary, step_summary
     out = {}
     with Executor(arena_bytes=4 << 30, flags=B.TG_OPT_TRACE_TASKS) as ex:
         for g in graphs:
@@ -577,6 +580,12 @@ def critical_path_trace(Executor, B, graphs, tuned):
             st, en, wh = B.tg_trace_copy(ex.ctx, h.handle, g.n)
             r = critical_path(g.src, g.dst, st, en, wh)
             r["traced_sched_ms"] = statistics.median(ts)
+            r["steps"] = step_summary(st, en, wh)
+            ids = np.arange(g.n, dtype=np.int64)
+            if "width" in g.meta:
+                r["levels"] = level_summary(ids // g.meta["width"], g.src, g.dst, st, en, wh)
+            elif "side" in g.meta:
+                r["levels"] = level_summary(ids // g.meta["side"] + ids % g.meta["side"], g.src, g.dst, st, en, wh)
             out[g.name] = r
             h.destroy()
             ex.set_launch()

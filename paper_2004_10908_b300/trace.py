@@ -1,5 +1,5 @@
 """Reading per-task trace records (TG_OPT_TRACE_TASKS) along a graph's
-critical path.
+critical path, step by step, and level by level.
 
 tg_trace_copy gives, for each task's last execution, when a warp took it
 from a queue, when that warp's step ended (before the step's new
@@ -64,4 +64,91 @@ def critical_path(src, dst, start_ns, end_ns, where) -> dict:
         "wait_mean_us": float(wait.mean()) / 1e3 if len(wait) else 0.0,
         "hops_by_source": by,
         "all_tasks_by_source": {name: int((frm == c).sum()) for c, name in enumerate(FROM_NAMES)},
+    }
+
+
+def _steps(start_ns, end_ns, where):
+    """The warp steps of a traced run: tasks sharing a block, a take time and
+    a step end.  Returns (block, take, end, tasks) per step and, per step,
+    how many steps of its block ran at its midpoint (itself included)."""
+    st = np.asarray(start_ns, np.int64)
+    en = np.asarray(end_ns, np.int64)
+    blk = (np.asarray(where, np.uint32) & 0xFFFF).astype(np.int64)
+    key = np.stack([blk, st, en], 1)
+    uk, cnt = np.unique(key, axis=0, return_counts=True)
+    sb, ss, se = uk[:, 0], uk[:, 1], uk[:, 2]
+    conc = np.zeros(len(uk), np.int64)
+    for b in np.unique(sb):
+        i = np.nonzero(sb == b)[0]
+        mid = (ss[i] + se[i]) // 2
+        conc[i] = np.searchsorted(np.sort(ss[i]), mid, "right") - np.searchsorted(np.sort(se[i]), mid, "right")
+    return sb, ss, se, cnt, conc
+
+
+def step_summary(start_ns, end_ns, where) -> dict:
+    """Step durations (microseconds) by the number of tasks in the step and
+    by the number of steps of the same block running at once."""
+    sb, ss, se, cnt, conc = _steps(start_ns, end_ns, where)
+    dur = (se - ss).astype(np.float64)
+    by_size = {}
+    for lo, hi in ((1, 1), (2, 4), (5, 9), (10, 16), (17, 24), (25, 32)):
+        m = (cnt >= lo) & (cnt <= hi)
+        if m.any():
+            by_size[f"{lo}-{hi}" if hi > lo else f"{lo}"] = {"steps": int(m.sum()), "dur_p50_us": _pct(dur[m], 50)}
+    by_conc = {}
+    for c in np.unique(conc):
+        m = conc == c
+        if m.sum() >= 50:
+            by_conc[int(c)] = {"steps": int(m.sum()), "dur_p50_us": _pct(dur[m], 50),
+                               "tasks_mean": float(cnt[m].mean())}
+    return {"steps": int(len(cnt)), "tasks_per_step_mean": float(cnt.mean()), "dur_p50_us": _pct(dur, 50),
+            "by_tasks_in_step": by_size, "by_block_steps_at_once": by_conc}
+
+
+def level_summary(level, src, dst, start_ns, end_ns, where) -> dict:
+    """A levelled graph (level[task], levels numbered from 0) read level by
+    level: when each level completed, how many blocks ran it, the largest
+    share one block took, where each level's last-ending task came from, and
+    the wait from ready (the last predecessor's step end; a source: taken at
+    once) to taken, by source.  Times in microseconds."""
+    level = np.asarray(level, np.int64)
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    st = np.asarray(start_ns, np.int64)
+    en = np.asarray(end_ns, np.int64)
+    wh = np.asarray(where, np.uint32)
+    frm = (wh >> 16).astype(np.int64)
+    blk = (wh & 0xFFFF).astype(np.int64)
+    n = len(st)
+    ready = st.copy()
+    has_pred = np.zeros(n, bool)
+    has_pred[dst] = True
+    ready[has_pred] = 0
+    np.maximum.at(ready, dst, en[src])
+    wait = (st - ready).astype(np.float64)
+    nl = int(level.max()) + 1
+    order = np.argsort(level, kind="stable")
+    bounds = np.searchsorted(level[order], np.arange(nl + 1))
+    lend = np.empty(nl, np.int64)
+    nblk = np.empty(nl, np.int64)
+    top = np.empty(nl, np.int64)
+    last_src = np.empty(nl, np.int64)
+    for l in range(nl):
+        i = order[bounds[l]:bounds[l + 1]]
+        lend[l] = en[i].max()
+        nblk[l] = len(np.unique(blk[i]))
+        top[l] = np.bincount(blk[i]).max()
+        last_src[l] = frm[i[np.argmax(en[i])]]
+    gap = np.diff(lend).astype(np.float64)
+    return {
+        "levels": nl,
+        "level_gap_us": {"mean": float(gap.mean()) / 1e3 if len(gap) else 0.0, "p50": _pct(gap, 50),
+                         "p90": _pct(gap, 90)},
+        "blocks_per_level": {"mean": float(nblk.mean()), "p10": float(np.percentile(nblk, 10)),
+                             "p90": float(np.percentile(nblk, 90))},
+        "largest_block_share": {"mean": float(top.mean()), "p90": float(np.percentile(top, 90))},
+        "last_task_of_level_from": {name: int((last_src == c).sum()) for c, name in enumerate(FROM_NAMES)},
+        "wait_ready_to_taken_by_source": {name: {"tasks": int((frm == c).sum()), "p50_us": _pct(wait[frm == c], 50),
+                                                 "p90_us": _pct(wait[frm == c], 90)}
+                                          for c, name in enumerate(FROM_NAMES) if (frm == c).any()},
     }

@@ -60,3 +60,34 @@ def test_a_task_that_did_not_run_is_refused():
     with pytest.raises(ValueError):
         critical_path([0], [1], np.array([5, 0]), np.array([6, 0]), rec([INJ, RING], [0, 0]))
     assert FROM_NAMES[STEAL] == "steal"
+
+
+def test_steps_are_grouped_and_their_overlaps_counted():
+    from paper_2004_10908_b300.trace import step_summary
+    # block 0: step A (tasks 0, 1: 100..300) and step B (task 2: 150..250) overlap;
+    # block 1: step C (task 3: 0..1000) runs alone
+    st = np.array([100, 100, 150, 1])
+    en = np.array([300, 300, 250, 1001])
+    s = step_summary(st, en, rec([RING, RING, RING, STEAL], [0, 0, 0, 1]))
+    assert s["steps"] == 3 and s["tasks_per_step_mean"] == pytest.approx(4 / 3)
+    assert s["by_tasks_in_step"]["1"]["steps"] == 2 and s["by_tasks_in_step"]["2-4"]["steps"] == 1
+    assert s["by_tasks_in_step"]["2-4"]["dur_p50_us"] == pytest.approx(0.2)
+
+
+def test_levels_gaps_blocks_and_waits():
+    from paper_2004_10908_b300.trace import level_summary
+    # two levels of two tasks: 0, 1 -> 2, 3 (every edge)
+    src, dst = [0, 0, 1, 1], [2, 3, 2, 3]
+    st = np.array([10, 20, 400, 700])
+    en = np.array([110, 300, 500, 800])
+    wh = rec([INJ, INJ, RING, STEAL], [0, 1, 0, 2])
+    lv = level_summary(np.array([0, 0, 1, 1]), src, dst, st, en, wh)
+    assert lv["levels"] == 2
+    assert lv["level_gap_us"]["mean"] == pytest.approx(0.5)        # 300 -> 800 ns
+    assert lv["blocks_per_level"]["mean"] == pytest.approx(2.0)
+    assert lv["largest_block_share"]["mean"] == pytest.approx(1.0)
+    assert lv["last_task_of_level_from"] == {"hand": 0, "ring": 0, "own_deque": 0, "steal": 1, "injection": 1}
+    # ready at 300 (the later predecessor): task 2 waited 100 ns, task 3 400 ns; sources 0
+    w_ = lv["wait_ready_to_taken_by_source"]
+    assert w_["ring"]["p50_us"] == pytest.approx(0.1) and w_["steal"]["p50_us"] == pytest.approx(0.4)
+    assert w_["injection"]["p50_us"] == pytest.approx(0.0)
