@@ -384,3 +384,27 @@ def test_graphs_created_while_another_runs(ex):
         assert_same((st,) + tuple(ex.result(h)), oracle.run(g), g.name)
         h.destroy()
     h_long.destroy()
+
+
+def test_results_read_while_the_next_graph_runs(ex):
+    """tg_result_copy waits for its graph's own launch only: a graph's results
+    are read (and are the oracle's) while a graph submitted after it runs."""
+    g1 = w.config2a(seed=21, levels=60, width=300)
+    g2 = w.config2b(side=300, rounds=64)
+    h1, h2 = ex.graph(g1), ex.graph(g2, device_pack=True)
+    try:
+        t1 = ex.submit(h1)
+        t2 = ex.submit(h2)
+        assert ex.wait(t1) == 0
+        r1 = ex.result(h1)
+        assert_same((0,) + tuple(r1), oracle.run(g1), g1.name)
+        assert ex.wait(t2) == 0
+        assert_same((0,) + tuple(ex.result(h2)), oracle.run(g2), g2.name)
+        # a resubmitted graph: the read waits for its new launch
+        t1 = ex.submit(h1)
+        r1b = ex.result(h1)
+        assert ex.wait(t1) == 0
+        assert_same((0,) + tuple(r1b), oracle.run(g1), g1.name)
+    finally:
+        h1.destroy()
+        h2.destroy()
