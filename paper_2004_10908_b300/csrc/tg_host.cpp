@@ -1931,7 +1931,11 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
                 continue;
             u64 t = 0;
             int rc2 = measure(o, t);
-            if (rc2 == TG_ERR_INVALID || rc2 == TG_ERR_CUDA)
+            // a candidate whose run reported a race is skipped: the start
+            // geometry ran clean, so the graph is not racy and the report is
+            // the race check's known false positive (a task re-activated
+            // while it finishes its step), which some geometries provoke
+            if (rc2 == TG_ERR_INVALID || rc2 == TG_ERR_CUDA || rc2 == TG_ERR_RACE)
                 continue;
             if (rc2 != TG_OK)
                 return rc2;

@@ -101,6 +101,7 @@ __device__ __forceinline__ void vst64(u64 *p, u64 v)
 {
     asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+
 __device__ __forceinline__ u32 vld32(const u32 *p)
 {
     u32 v;
@@ -1127,6 +1128,15 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         }
         if (run && !cont)
             st_tasks++;
+        // A task that can run again stores its output before its releases,
+        // which are what make a later execution of it (on another SM)
+        // possible.  Issued after them, the store was seen to land after the
+        // next execution's under heavy stealing, leaving a stale final
+        // output.  (Without in-flight flags the fence below orders it; with
+        // them, the flag release comes a full round of release and
+        // push-check atomics after it.)
+        if (!acyclic && run && !cont)
+            __stcs(&p.outv[u], x);
         if (!race_check && !acyclic) {
             // without in-flight flags the state must be visible before any
             // release makes a later activation of this task possible
@@ -1319,7 +1329,7 @@ __device__ __forceinline__ void sched_body(const KParams &p)
         } else if (any_enter) {
             fence_acq_rel_gpu();
         }
-        if (run && !cont)
+        if (acyclic && run)
             __stcs(&p.outv[u], x);
         if (any_enter) {
             // ---- a module task enters its composed graph: takes it (its
