@@ -183,8 +183,8 @@ def run_reference(args):
 # describe the kernel source they were taken on, so they are reported only
 # while tg_kernels.cu still has that hash.
 MEASURED_TRAFFIC = {
-    "kernels_sha256": "624907b0238247eada04a59ef258a050f29ba5e0b27cf118ed847eb317701e71",
-    "bytes_per_launch": {"config2a": 52_770_000, "config2b": 44_470_000},
+    "kernels_sha256": "1bd7644b9a978660a5343dc97203a125abf6be992341d14913111b1f4ebd5178",
+    "bytes_per_launch": {"config2a": 52_670_000, "config2b": 44_530_000},
 }
 
 
@@ -419,7 +419,8 @@ def plain_single_graph(Executor, torch, B):
 def condition_heavy(Executor, torch, peaks, atom_ceiling):
     """The condition-heavy graph: exactly 10,000 condition tasks in lanes of
     loops nested 3 deep, branch conditions over 2-4 arms, 100-task bodies,
-    32 rounds (522,764 tasks, 106.5 M executions).  Device time, tasks/s,
+    32 rounds (522,764 tasks, 106.5 M executions), at its autotuned launch
+    geometry.  Device time, tasks/s,
     the payload-only ALU ceiling on the same execution count at 32 rounds,
     the release atomics per second against the measured atomic ceiling, the
     oracle on one host core, and an element-by-element check."""
@@ -430,6 +431,10 @@ def condition_heavy(Executor, torch, peaks, atom_ceiling):
     oracle_s = time.perf_counter() - t0
     with Executor(arena_bytes=1 << 30) as ex:
         h = ex.graph(g)
+        # its own launch geometry, as the headline graphs get theirs
+        t_tune = time.perf_counter()
+        tuned, _ = ex.autotune(h, trials=1)
+        tune_s = time.perf_counter() - t_tune
         ts = []
         for _ in range(3):
             assert ex.run(h) == 0
@@ -452,6 +457,10 @@ def condition_heavy(Executor, torch, peaks, atom_ceiling):
     return {"workload": "condition-heavy: 10,000 condition tasks, loops nested 3 deep, branch over k in {2,3,4} "
                         "arms, 10 x 10 bodies (d~U{1..4}), 32 rounds; seed 3",
             "tasks": g.n, "edges": g.m, "executions": ref.execs, "sched_ms": sched_ns / 1e6,
+            "launch_geometry": {k: tuned[k] for k in ("worker_blocks", "warps_per_block", "batch_max", "local_keep",
+                                                      "max_thieves", "steal_policy", "max_steal", "keep_idle",
+                                                      "hand_batch", "steal_backoff_ns", "idle_sleep_ns")},
+            "autotune_s": tune_s,
             "tasks_s": ref.execs / (sched_ns * 1e-9), "ns_per_task": sched_ns / ref.execs,
             "payload_only_ms": pay_ns / 1e6, "alu_frac_of_payload_ceiling": pay_ns / sched_ns,
             "alu_frac_of_int_peak": 9 * 32 * ref.execs / (sched_ns * 1e-9) / alu_peak,
