@@ -1919,6 +1919,10 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
     const int idle_c[] = {128, 256, 1024};
     const int keep_idle_c[] = {0, 1};
     const int hand_batch_c[] = {0, 1};
+    // every candidate measured, for the confirmation below
+    std::vector<std::pair<u64, tg_ctx_opts>> seen;
+    if (best_t)
+        seen.push_back({best_t, best});
     auto try_knob = [&](auto setter, const int *vals, int nv) -> int {
         for (int i = 0; i < nv; ++i) {
             tg_ctx_opts o = best;
@@ -1939,6 +1943,8 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
                 continue;
             if (rc2 != TG_OK)
                 return rc2;
+            if (t)
+                seen.push_back({t, o});
             if (t && t < best_t) {
                 best_t = t;
                 best = o;
@@ -1966,6 +1972,37 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
             return rc;
         if (best_t >= pass_t)
             break;
+    }
+    // Confirmation: a single measurement per candidate is a few percent
+    // noisy, about what separates the best geometries of a graph, so the
+    // three fastest distinct candidates are measured once more and the pick
+    // is the fastest by the sum of both measurements.
+    std::sort(seen.begin(), seen.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
+    std::vector<std::pair<u64, tg_ctx_opts>> top;
+    for (const auto &cand : seen) {
+        bool dup = false;
+        for (const auto &t : top)
+            dup = dup || std::memcmp(&t.second, &cand.second, sizeof(tg_ctx_opts)) == 0;
+        if (!dup)
+            top.push_back(cand);
+        if (top.size() == 3)
+            break;
+    }
+    if (top.size() > 1) {
+        u64 best_sum = ~0ull;
+        for (const auto &cand : top) {
+            u64 t2 = 0;
+            const int rc3 = measure(cand.second, t2);
+            if (rc3 == TG_ERR_INVALID || rc3 == TG_ERR_CUDA || rc3 == TG_ERR_RACE || !t2)
+                continue;
+            if (rc3 != TG_OK)
+                return rc3;
+            if (cand.first + t2 < best_sum) {
+                best_sum = cand.first + t2;
+                best = cand.second;
+                best_t = std::min(cand.first, t2);
+            }
+        }
     }
     if (cache_path) {
         if (FILE *f = std::fopen(cache_path, "a")) {
