@@ -1938,8 +1938,10 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
             // a candidate whose run reported a race is skipped: the start
             // geometry ran clean, so the graph is not racy and the report is
             // the race check's known false positive (a task re-activated
-            // while it finishes its step), which some geometries provoke
-            if (rc2 == TG_ERR_INVALID || rc2 == TG_ERR_CUDA || rc2 == TG_ERR_RACE)
+            // while it finishes its step), which some geometries provoke; so
+            // is one that ran into the time limit (adaptive thieves over many
+            // small blocks can be two orders of magnitude slower)
+            if (rc2 == TG_ERR_INVALID || rc2 == TG_ERR_CUDA || rc2 == TG_ERR_RACE || rc2 == TG_ERR_TIMEOUT)
                 continue;
             if (rc2 != TG_OK)
                 return rc2;
@@ -1993,7 +1995,7 @@ static int tune_geometry(tg_ctx *c, const std::string &key, const char *cache_pa
         for (const auto &cand : top) {
             u64 t2 = 0;
             const int rc3 = measure(cand.second, t2);
-            if (rc3 == TG_ERR_INVALID || rc3 == TG_ERR_CUDA || rc3 == TG_ERR_RACE || !t2)
+            if (rc3 == TG_ERR_INVALID || rc3 == TG_ERR_CUDA || rc3 == TG_ERR_RACE || rc3 == TG_ERR_TIMEOUT || !t2)
                 continue;
             if (rc3 != TG_OK)
                 return rc3;
