@@ -195,6 +195,8 @@ int tg_graph_create(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const u
  * 29 bytes per task and 17 per edge, allocated on first use and grown when a
  * larger graph comes (TG_ERR_BUDGET if that allocation fails); it is freed
  * with the context.  Uses the side stream; complete when the call returns.
+ * While the resident server runs, the packing kernels share the SMs with it
+ * (its blocks leave part of each SM free for side-stream work).
  * tg_graph_get_info: pack_ns = device time of validation and packing,
  * upload_ns = device time of the input copies. */
 int tg_graph_create_dev(tg_ctx *ctx, uint32_t n_nodes, const uint8_t *kinds, const uint32_t *params,
