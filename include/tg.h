@@ -502,6 +502,18 @@ int tg_trace_copy(tg_ctx *ctx, const tg_graph *g, uint64_t *start_ns, uint64_t *
  * *len receives the text's length (without the terminating NUL); the text is
  * written only if buf holds len + 1 bytes, else TG_ERR_BUDGET. */
 int tg_graph_dot(tg_ctx *ctx, const tg_graph *g, char *buf, size_t cap, size_t *len);
+/* The packed form of g word for word, as the device holds it (for tests and
+ * debugging).  records[8 * n] receives each task's 32-byte record: successor
+ * offset (relative to the graph's first successor entry), successor count |
+ * strong in-degree << 16, rounds | kind << 16 | argument << 24, task id, join
+ * word (low word first), execution count, digest.  edges receives the
+ * graph's successor entries (graph-local ids; bit 31 marks a task's only
+ * strong in-edge; a module or subflow task's list is led by a graph slot id)
+ * followed by its source list; *edge_words (if not NULL) receives their
+ * count.  Either array may be NULL.  Synchronises the context stream unless
+ * the resident server runs. */
+int tg_graph_packed_copy(tg_ctx *ctx, const tg_graph *g, uint32_t *records, uint32_t *edges,
+                         uint64_t *edge_words);
 
 const char *tg_strerror(int status);
 

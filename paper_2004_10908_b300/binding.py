@@ -82,6 +82,7 @@ SIGNATURES = {
     "tg_ctx_destroy": (ctypes.c_int, [_vp]),
     "tg_graph_create": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, ctypes.POINTER(_vp)]),
     "tg_graph_create_dev": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, ctypes.POINTER(_vp)]),
+    "tg_graph_packed_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(_u64)]),
     "tg_graph_autotune": (ctypes.c_int, [_vp, _vp, _u32, ctypes.c_char_p, ctypes.POINTER(tg_ctx_opts),
                                          ctypes.POINTER(_u64)]),
     "tg_graph_create_composed": (ctypes.c_int, [_vp, _u32, _vp, _vp, _u32, _vp, _vp, _vp, _u32, _vp,
@@ -388,6 +389,18 @@ def tg_stream_plan(n, src, dst, max_streams):
     st = load().tg_stream_plan(n, len(s), sp, dp, max_streams, stream.ctypes.data_as(_vp), ctypes.byref(ne),
                                ctypes.byref(nw))
     return st, stream, ne.value, nw.value
+
+
+def tg_graph_packed_copy(ctx, g, n):
+    """The packed graph word for word: (records as an (n, 8) uint32 array,
+    successor entries followed by the source list)."""
+    words = _u64(0)
+    _check(load().tg_graph_packed_copy(_vp(ctx), _vp(g), None, None, ctypes.byref(words)), "tg_graph_packed_copy")
+    rec = np.empty((n, 8), np.uint32)
+    edges = np.empty(words.value, np.uint32)
+    _check(load().tg_graph_packed_copy(_vp(ctx), _vp(g), rec.ctypes.data_as(_vp), edges.ctypes.data_as(_vp), None),
+           "tg_graph_packed_copy")
+    return rec, edges
 
 
 def tg_graph_dot(ctx, g) -> str:

@@ -1454,6 +1454,25 @@ int tg_stream_plan(uint32_t n, uint32_t m, const uint32_t *src, const uint32_t *
     return TG_OK;
 }
 
+int tg_graph_packed_copy(tg_ctx *c, const tg_graph *g, uint32_t *records, uint32_t *edges, uint64_t *edge_words)
+{
+    if (!c || !g || g->ctx != c)
+        return TG_ERR_INVALID;
+    const tg_graph *t = g->tmpl ? g->tmpl : g;   // an instance shares its template's lists
+    if (edge_words)
+        *edge_words = t->edge_len;
+    if (!c->serving)
+        TG_CUDA(cudaStreamSynchronize(c->stream));
+    if (records) {
+        TG_CUDA(cudaMemcpy(records, c->slots + g->node_off, (size_t)g->n * sizeof(NodeSlot), cudaMemcpyDeviceToHost));
+        for (u32 v = 0; v < g->n; ++v)
+            records[8ull * v] -= (u32)t->edge_off;
+    }
+    if (edges && t->edge_len)
+        TG_CUDA(cudaMemcpy(edges, c->edges + t->edge_off, (size_t)t->edge_len * 4, cudaMemcpyDeviceToHost));
+    return TG_OK;
+}
+
 int tg_graph_dot(tg_ctx *c, const tg_graph *g, char *buf, size_t cap, size_t *len)
 {
     if (!c || !g || g->ctx != c || !len)

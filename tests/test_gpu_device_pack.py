@@ -51,6 +51,12 @@ def test_same_packed_graph_and_oracle_results(ex):
         gd = ex.graph(g, device_pack=True)
         try:
             assert B.tg_graph_dot(ex.ctx, gd.handle) == B.tg_graph_dot(ex.ctx, gh.handle), g.name
+            # word for word: records (successor offsets relative to the graph's
+            # lists), successor entries with their flags, source list
+            rh, eh = B.tg_graph_packed_copy(ex.ctx, gh.handle, g.n)
+            rd, ed = B.tg_graph_packed_copy(ex.ctx, gd.handle, g.n)
+            np.testing.assert_array_equal(rd, rh, err_msg=f"{g.name}: records")
+            np.testing.assert_array_equal(ed, eh, err_msg=f"{g.name}: successor and source lists")
             ih, idv = gh.info(), gd.info()
             for k in ("n_nodes", "n_edges", "n_sources", "n_conditions", "device_bytes"):
                 assert ih[k] == idv[k], (g.name, k)
@@ -161,7 +167,11 @@ def test_random_graphs_valid_and_invalid(ex):
         try:
             assert st_d == st_h, (t, B.STATUS_NAMES[st_d], B.STATUS_NAMES[st_h])
             if st_h == B.TG_OK:
-                assert B.tg_graph_dot(ex.ctx, d) == B.tg_graph_dot(ex.ctx, h), t
+                n = len(kinds)
+                rh, eh = B.tg_graph_packed_copy(ex.ctx, h, n)
+                rd, ed = B.tg_graph_packed_copy(ex.ctx, d, n)
+                np.testing.assert_array_equal(rd, rh, err_msg=f"graph {t}: records")
+                np.testing.assert_array_equal(ed, eh, err_msg=f"graph {t}: lists")
                 created += 1
         finally:
             for x in (h, d):
